@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs of the FCGLE workloads (shared by tests, bench, smoke).
+
+This module holds no arithmetic of the time-stepping method: only grids,
+initial data drawn from seeded generators, and the closed-form continuous
+source terms s(t, x) of manufactured exact solutions (they are part of the
+problem statement, Eq. FCGLE, not of its discretisation).
+
+Arrays are numpy, shape (n_d, ..., n_1), C order, i.e. vec order with j_1
+fastest (Sec. 2, Eq. indexj); complex128 unless stated.
+
+Workloads (recipes; sizes as in the paper's 2D/3D experiments):
+* ``gaussian_manufactured``: u = (1+i) e^{-t} exp(-|x|^2) on (-10,10)^d with
+  its continuous source s = e^{-t} S_1 + e^{-3t} S_3.
+* ``sech_pulse_noise``: sech(|x|) e^{0.5 i x_1} + uniform noise of amplitude
+  1e-3 in re and im (PCG64, drawn in vec order).
+* ``gaussian_random_phase``: exp(-|x|^2) e^{i pi xi}, xi white noise (PCG64)
+  smoothed by a separable Gaussian filter of standard deviation ``corr``
+  physical units (zero padded), then standardised.
+* ``polynomial_manufactured``: the paper's Example 1,
+  u = e^{-i t} prod_mu (1 - x_mu^2)^4 on (-1,1)^d, with its continuous source.
+"""
+import math
+
+import numpy as np
+
+
+def grid(n, a, b):
+    h = (b - a) / (n + 1)
+    return a + h * np.arange(1, n + 1, dtype=np.float64), h
+
+
+def mesh(ns, boxes):
+    """Coordinates [X_1, ..., X_d], each of shape (n_d, ..., n_1)."""
+    xs = [grid(n, a, b)[0] for n, (a, b) in zip(ns, boxes)]
+    return np.meshgrid(*reversed(xs), indexing="ij")[::-1]
+
+
+# ---------------------------------------------------------------------------
+# Riesz derivatives of the 1D profiles (Sec. 1 definitions)
+# ---------------------------------------------------------------------------
+
+def riesz_gaussian(x, alpha):
+    """Riesz derivative of exp(-x^2): the inverse Fourier transform of
+    -|xi|^alpha sqrt(pi) exp(-xi^2/4), i.e.
+    -2^alpha Gamma((1+alpha)/2)/sqrt(pi) * 1F1((1+alpha)/2; 1/2; -x^2).
+    Kummer's transformation keeps 1F1 well scaled for large x^2."""
+    from scipy.special import hyp1f1, gamma
+    a = (1.0 + alpha) / 2.0
+    x2 = np.asarray(x, dtype=np.float64) ** 2
+    f = np.exp(-x2) * hyp1f1(0.5 - a, 0.5, x2)
+    big = x2 > 80.0
+    if np.any(big):
+        # large-argument form of 1F1(a; 1/2; -x^2) (DLMF 13.7.2 leading terms)
+        z = x2[big]
+        s = np.zeros_like(z)
+        term = np.ones_like(z)
+        pref = gamma(0.5) / gamma(0.5 - a)
+        for k in range(0, 12):
+            s += term
+            term = term * (a + k) * (a + 0.5 + k) / ((k + 1) * z)
+        f[big] = pref * z ** (-a) * s
+    return -(2.0 ** alpha) * gamma(a) / math.sqrt(math.pi) * f
+
+
+def _poly_coeffs_y():
+    """Coefficients c_m of (1-x^2)^4 = y^4 (2-y)^4 in powers of y = 1+x."""
+    c = np.zeros(9)
+    for j in range(5):
+        c[4 + j] = math.comb(4, j) * 2.0 ** (4 - j) * (-1.0) ** j
+    return c
+
+
+def riesz_poly(x, alpha):
+    """Riesz derivative of w(x) = (1-x^2)^4 on (-1,1), zero outside, for
+    |x| < 1: -1/(2 cos(alpha pi/2)) (D_left + D_right) with the
+    Riemann-Liouville power rule D^alpha y^m = Gamma(m+1)/Gamma(m+1-alpha) y^{m-alpha}
+    applied in y = 1+x (left) and y = 1-x (right)."""
+    from scipy.special import gamma
+    x = np.asarray(x, dtype=np.float64)
+    c = _poly_coeffs_y()
+    yl, yr = 1.0 + x, 1.0 - x
+    acc = np.zeros_like(x)
+    for m in range(4, 9):
+        k = gamma(m + 1.0) / gamma(m + 1.0 - alpha)
+        acc += c[m] * k * (yl ** (m - alpha) + yr ** (m - alpha))
+    return -acc / (2.0 * math.cos(alpha * math.pi / 2.0))
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def gaussian_manufactured(ns, boxes, alphas, nu, eta, gamma, kappa, zeta):
+    """u(t) = (1+i) e^{-t} G, G = exp(-|x|^2); returns (u0, sigmas, [S_1, S_3])
+    with s(t, x) = e^{-t} S_1 + e^{-3t} S_3 the continuous source:
+    S_1 = (1+i)(-(1+gamma) G - (nu+i eta) sum_mu R_mu(x_mu) prod_{nu!=mu} g(x_nu)),
+    S_3 = 2 (1+i)(kappa + i zeta) G^3."""
+    X = mesh(ns, boxes)
+    gs = [np.exp(-Xm ** 2) for Xm in X]
+    G = np.prod(gs, axis=0)
+    lap = np.zeros_like(G)
+    for mu in range(len(ns)):
+        term = riesz_gaussian(X[mu], alphas[mu])
+        for o in range(len(ns)):
+            if o != mu:
+                term = term * gs[o]
+        lap += term
+    c = nu + 1j * eta
+    S1 = (1 + 1j) * (-(1.0 + gamma) * G - c * lap)
+    S3 = 2.0 * (1 + 1j) * (kappa + 1j * zeta) * G ** 3
+    u0 = (1 + 1j) * G
+    return u0.astype(np.complex128), [-1.0, -3.0], [S1, S3]
+
+
+def gaussian_exact(ns, boxes, t):
+    X = mesh(ns, boxes)
+    return (1 + 1j) * math.exp(-t) * np.exp(-sum(Xm ** 2 for Xm in X))
+
+
+def polynomial_manufactured(ns, alphas, nu, eta, gamma, kappa, zeta):
+    """Example 1 of the paper: u = e^{-i t} W, W = prod_mu (1 - x_mu^2)^4 on (-1,1)^d.
+    s(t, x) = e^{-i t} S with
+    S = (-i - gamma) W - (nu + i eta) sum_mu R_mu(x_mu) prod_{nu != mu} w(x_nu) + (kappa + i zeta) W^3."""
+    boxes = [(-1.0, 1.0)] * len(ns)
+    X = mesh(ns, boxes)
+    ws = [(1.0 - Xm ** 2) ** 4 for Xm in X]
+    W = np.prod(ws, axis=0)
+    lap = np.zeros_like(W)
+    for mu in range(len(ns)):
+        term = riesz_poly(X[mu], alphas[mu])
+        for o in range(len(ns)):
+            if o != mu:
+                term = term * ws[o]
+        lap += term
+    S = (-1j - gamma) * W - (nu + 1j * eta) * lap + (kappa + 1j * zeta) * W ** 3
+    return W.astype(np.complex128), [-1j], [S.astype(np.complex128)]
+
+
+def polynomial_exact(ns, t):
+    X = mesh(ns, [(-1.0, 1.0)] * len(ns))
+    return np.exp(-1j * t) * np.prod([(1.0 - Xm ** 2) ** 4 for Xm in X], axis=0)
+
+
+def sech_pulse_noise(ns, boxes, seed=0, amp=1e-3, k1=0.5):
+    X = mesh(ns, boxes)
+    r = np.sqrt(sum(Xm ** 2 for Xm in X))
+    u = (1.0 / np.cosh(r)) * np.exp(1j * k1 * X[0])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = u.size
+    re = rng.uniform(-amp, amp, N)
+    im = rng.uniform(-amp, amp, N)
+    return (u + (re + 1j * im).reshape(u.shape)).astype(np.complex128)
+
+
+def gaussian_random_phase(ns, boxes, seed=1, corr=1.0):
+    from scipy.ndimage import gaussian_filter1d
+    X = mesh(ns, boxes)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xi = rng.standard_normal(X[0].shape)
+    for mu, (n, (a, b)) in enumerate(zip(ns, boxes)):
+        h = (b - a) / (n + 1)
+        xi = gaussian_filter1d(xi, sigma=corr / h, axis=len(ns) - 1 - mu,
+                               mode="constant", cval=0.0, truncate=4.0)
+    xi = (xi - xi.mean()) / xi.std()
+    u = np.exp(-sum(Xm ** 2 for Xm in X)) * np.exp(1j * math.pi * xi)
+    return u.astype(np.complex128)
+
+
+def gaussian_pulse(ns, boxes):
+    X = mesh(ns, boxes)
+    return np.exp(-sum(Xm ** 2 for Xm in X)).astype(np.complex128)
