@@ -1,0 +1,172 @@
+/*
+ * fcgle.h -- C ABI of the GB300 (sm_103a) FCGLE time-stepping library.
+ *
+ * The library advances the semidiscrete space-fractional complex
+ * Ginzburg--Landau equation (paper Eq. FCGLE, Sec. 2)
+ *
+ *     u'(t) = K u(t) + g(t, u(t)),     (Eq. ODEs)
+ *     K = A_d (+) ... (+) A_1,  A_mu = (nu + i eta) D_mu      (Eq. Ksum)
+ *     g(t, u) = gamma u - (kappa + i zeta)|u|^2 u + s(t)      (Sec. 2)
+ *
+ * by applying f(theta K) directly through the eigendecompositions
+ * D_mu = Q_mu Lam_mu Q_mu^T (Eq. diag): the Tucker form
+ *     f(theta K) v = ((F o (V x_1 Q_1^T ... x_d Q_d^T)) x_1 Q_1 ... x_d Q_d)   (Eq. fKu_diag)
+ * and, for f = exp, the Kronecker-product form
+ *     exp(theta K) v = V x_1 exp(theta A_1) ... x_d exp(theta A_d)            (Eq. Neudeckerd).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tensors.  A solution tensor is N = n_1 * ... * n_d complex numbers,
+ *   interleaved (re, im), in vec order with j_1 fastest (Eq. indexj):
+ *   element (j_1, .., j_d) (0-based) is at j_1 + n_1 (j_2 + n_2 j_3).
+ *   Element type: complex128 (two doubles) for FCGLE_FP64 handles,
+ *   complex64 (two floats) for FCGLE_BF16X3 handles.  Pointers are DEVICE
+ *   pointers unless the function name ends in _host.  The caller owns every
+ *   tensor it passes; the library keeps no pointer to it after the call
+ *   returns, except the source tensors, which are copied at set time.
+ * Streams.  Every device entry point is asynchronous on the handle's CUDA
+ *   stream (given at setup, changeable with fcgle_set_stream); the caller
+ *   synchronises.  _host entry points synchronise before returning.
+ * Errors.  Every function returns an fcgle_status; nothing throws across the
+ *   ABI.  On error, fcgle_last_error() returns a thread-local message.
+ *   Invalid parameters (d not in 1..3, n_mu < 1, alpha_mu not in (1,2),
+ *   nu <= 0, kappa <= 0, b_mu <= a_mu, fd_order not in {2,4}, unknown enum
+ *   values, null pointers) give FCGLE_ERR_INVALID_ARG and leave the handle
+ *   unchanged.  A CUDA failure gives FCGLE_ERR_CUDA; the handle must then be
+ *   destroyed.
+ * Memory.  fcgle_setup allocates every device buffer the handle needs for
+ *   apply_f and the one-step schemes; the spectral scalar tensors of a given
+ *   (scheme, tau) are allocated and filled once, on first use (outside any
+ *   time loop), and cached on the handle until fcgle_destroy.
+ */
+#ifndef FCGLE_H
+#define FCGLE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FCGLE_OK = 0,
+  FCGLE_ERR_INVALID_ARG = 1,
+  FCGLE_ERR_NOMEM = 2,
+  FCGLE_ERR_CUDA = 3,
+  FCGLE_ERR_NUMERIC = 4,     /* eigendecomposition residual too large, non-finite state */
+  FCGLE_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  FCGLE_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} fcgle_status;
+
+/* Arithmetic of the mode products.  FCGLE_FP64: complex128 tensors, FP64
+ * mode products.  FCGLE_BF16X3: complex64 tensors (FP32 storage), mode
+ * products on the tcgen05 tensor cores with each FP32 operand split as
+ * hi + lo (two bf16) and hi*hi + hi*lo + lo*hi accumulated in FP32; the
+ * eigendecomposition and the phi/exp scalars stay FP64. */
+typedef enum { FCGLE_FP64 = 0, FCGLE_BF16X3 = 2 } fcgle_precision;
+
+/* f in f(theta K): (1 - z)^{-1}, e^z, phi_k(z) (Eq. phi). */
+typedef enum { FCGLE_F_INV = 0, FCGLE_F_EXP = 1, FCGLE_F_PHI = 2 } fcgle_func;
+
+/* Time integrators.  LIE: linearly-implicit Euler (Eq. lbdf2-v, first step).
+ * LBDF2: linearised BDF2 (Eq. lbdf2-v).  KROGSTAD: Krogstad's exponential
+ * RK4 (Eq. krogstad-v).  STRANG: Strang splitting with the exact nonlinear
+ * flow (Eq. Strang; source ignored).  LAWSON_EULER, LAWSON_RK2 (Heun-based)
+ * and ETD2RK (Cox-Matthews) are not in the paper; their definitions are the
+ * ones of the oracle's scheme module. */
+typedef enum {
+  FCGLE_LIE = 0,
+  FCGLE_LAWSON_EULER = 1,
+  FCGLE_LAWSON_RK2 = 2,
+  FCGLE_ETD2RK = 3,
+  FCGLE_KROGSTAD = 4,
+  FCGLE_LBDF2 = 5,
+  FCGLE_STRANG = 6
+} fcgle_scheme;
+
+/* Problem statement (Eq. FCGLE, Sec. 2): d directions, n_mu interior points
+ * on (a_mu, b_mu) with h_mu = (b_mu - a_mu)/(n_mu + 1), Riesz orders alpha_mu,
+ * finite differences of order 2 (Eq. FD2) or 4 (Eq. FD4).  Entries mu >= d
+ * are ignored. */
+typedef struct {
+  int d;
+  int n[3];
+  double a[3];
+  double b[3];
+  double alpha[3];
+  double nu, eta, gamma, kappa, zeta;
+  int fd_order;   /* 2 or 4 */
+  int precision;  /* fcgle_precision */
+} fcgle_params;
+
+typedef struct fcgle_ctx* fcgle_handle;
+
+/* Builds D_mu (Eq. Dnalpha / Eq. FD4), eigendecomposes each in FP64 on the
+ * host (Householder tridiagonalisation + implicit QL with Wilkinson shifts),
+ * checks ||D Q - Q Lam|| and ||Q^T Q - I|| (FCGLE_ERR_NUMERIC if above
+ * 1e-11 relative), copies Q_mu and lam_mu to the device once (Sec. 4.2: the
+ * only host-to-device transfer of the method) and allocates the work
+ * buffers.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns everything; release it with fcgle_destroy. */
+fcgle_status fcgle_setup(const fcgle_params* params, void* cuda_stream, fcgle_handle* out);
+
+/* Replaces the handle's stream (cudaStream_t). */
+fcgle_status fcgle_set_stream(fcgle_handle h, void* cuda_stream);
+
+/* Source term s(t, x) = sum_k exp(sigma_k t) S_k(x), sigma_k complex
+ * (sigma_reim[2k] + i sigma_reim[2k+1]).  S_dev[k] are device tensors in the
+ * user layout; they are copied into the handle (the caller may free them
+ * afterwards).  nterms = 0 removes the source.  At most 4 terms. */
+fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_reim,
+                              const void* const* S_dev);
+
+/* out = f(theta K) v with f = 1/(1-z) (func INV), e^z (EXP, Eq. Neudeckerd)
+ * or phi_k (PHI, k in 0..4).  v and out are device tensors in the user layout
+ * and may alias. */
+fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta,
+                           const void* v, void* out);
+
+/* One step of a one-step scheme (every scheme except LBDF2), in place:
+ * u <- step(t, u) with step size tau > 0. */
+fcgle_status fcgle_step(fcgle_handle h, int scheme, double tau, double t, void* u);
+
+/* nsteps >= 0 constant steps of size tau from (t0, u0); the result goes to
+ * uT (u0 and uT may alias).  LBDF2 starts with one LIE step (Eq. lbdf2-v). */
+fcgle_status fcgle_integrate(fcgle_handle h, int scheme, double tau, int nsteps, double t0,
+                             const void* u0, void* uT);
+
+/* As fcgle_integrate with HOST buffers: copies u0 host -> device, integrates,
+ * copies the result device -> host and synchronises the stream. */
+fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int nsteps, double t0,
+                                  const void* u0_host, void* uT_host);
+
+/* Discrete L2 norm (prod_mu h_mu sum_j |u_j|^2)^{1/2} (Sec. 4) of a device
+ * tensor, written to *out_host (synchronises the stream). */
+fcgle_status fcgle_norm(fcgle_handle h, const void* u, double* out_host);
+
+/* Synchronises the handle's stream and reports device-side failures of the
+ * work enqueued so far: FCGLE_ERR_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up (its output is then invalid), FCGLE_ERR_CUDA on
+ * an asynchronous CUDA error. */
+fcgle_status fcgle_sync(fcgle_handle h);
+
+/* Sizes: N (complex elements of a user tensor) and the bytes of one user
+ * tensor. */
+fcgle_status fcgle_sizes(fcgle_handle h, size_t* n_elems, size_t* n_bytes);
+
+/* Number of kernel launches this handle has issued since setup (all
+ * entry points; used to report launch counts). */
+fcgle_status fcgle_launch_count(fcgle_handle h, long long* count);
+
+fcgle_status fcgle_destroy(fcgle_handle h);
+
+const char* fcgle_status_string(fcgle_status s);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* fcgle_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCGLE_H */

@@ -1,0 +1,237 @@
+// C ABI entry points (include/fcgle.h): argument validation, exception to
+// status translation and the thread-local error message.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "engine.h"
+
+struct fcgle_ctx {
+  fcgle_params prm;
+  cudaStream_t stream = nullptr;
+  std::unique_ptr<fcgle::EngineBase> eng;
+};
+
+namespace fcgle {
+
+static thread_local std::string g_last_error;
+
+void throw_cuda(cudaError_t e, const char* where) {
+  throw CudaError{e, std::string(where) + ": " + cudaGetErrorString(e)};
+}
+
+namespace {
+
+fcgle_status fail(fcgle_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+template <typename F>
+fcgle_status guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    f();
+    return FCGLE_OK;
+  } catch (const InvalidArg& e) {
+    return fail(FCGLE_ERR_INVALID_ARG, e.what());
+  } catch (const Unsupported& e) {
+    return fail(FCGLE_ERR_UNSUPPORTED, e.what());
+  } catch (const NumericError& e) {
+    return fail(FCGLE_ERR_NUMERIC, e.what());
+  } catch (const DeviceTimeout& e) {
+    return fail(FCGLE_ERR_TIMEOUT, e.what());
+  } catch (const CudaError& e) {
+    if (e.err == cudaErrorMemoryAllocation) return fail(FCGLE_ERR_NOMEM, e.where);
+    return fail(FCGLE_ERR_CUDA, e.where);
+  } catch (const std::bad_alloc&) {
+    return fail(FCGLE_ERR_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(FCGLE_ERR_CUDA, e.what());
+  }
+}
+
+void validate(const fcgle_params* p) {
+  if (!p) throw InvalidArg("params is NULL");
+  if (p->d < 1 || p->d > 3) throw InvalidArg("d must be 1, 2 or 3");
+  for (int mu = 0; mu < p->d; ++mu) {
+    if (p->n[mu] < 1) throw InvalidArg("n_mu must be >= 1");
+    if (p->n[mu] > 8192) throw InvalidArg("n_mu must be <= 8192");
+    if (!(p->alpha[mu] > 1.0 && p->alpha[mu] < 2.0)) throw InvalidArg("alpha_mu must lie in (1, 2)");
+    if (!(p->b[mu] > p->a[mu])) throw InvalidArg("b_mu must exceed a_mu");
+  }
+  if (!(p->nu > 0.0)) throw InvalidArg("nu must be positive");
+  if (!(p->kappa > 0.0)) throw InvalidArg("kappa must be positive");
+  if (!std::isfinite(p->eta) || !std::isfinite(p->gamma) || !std::isfinite(p->zeta))
+    throw InvalidArg("eta, gamma, zeta must be finite");
+  if (p->fd_order != 2 && p->fd_order != 4) throw InvalidArg("fd_order must be 2 or 4");
+  if (p->precision != FCGLE_FP64 && p->precision != FCGLE_BF16X3) throw InvalidArg("unknown precision");
+}
+
+void check_handle(fcgle_handle h) {
+  if (!h || !h->eng) throw InvalidArg("invalid handle");
+}
+
+void check_scheme(int scheme) {
+  if (scheme < FCGLE_LIE || scheme > FCGLE_STRANG) throw InvalidArg("unknown scheme");
+}
+
+void check_tau(double tau) {
+  if (!(tau > 0.0) || !std::isfinite(tau)) throw InvalidArg("tau must be positive and finite");
+}
+
+}  // namespace
+}  // namespace fcgle
+
+using namespace fcgle;
+
+extern "C" {
+
+fcgle_status fcgle_setup(const fcgle_params* params, void* cuda_stream, fcgle_handle* out) {
+  return guarded([&] {
+    if (!out) throw InvalidArg("out is NULL");
+    *out = nullptr;
+    validate(params);
+    auto* ctx = new fcgle_ctx;
+    try {
+      ctx->prm = *params;
+      ctx->stream = (cudaStream_t)cuda_stream;
+      ctx->eng = make_engine(*params, ctx->stream);
+    } catch (...) {
+      delete ctx;
+      throw;
+    }
+    *out = ctx;
+  });
+}
+
+fcgle_status fcgle_set_stream(fcgle_handle h, void* cuda_stream) {
+  return guarded([&] {
+    check_handle(h);
+    h->stream = (cudaStream_t)cuda_stream;
+    h->eng->set_stream(h->stream);
+  });
+}
+
+fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_reim, const void* const* S_dev) {
+  return guarded([&] {
+    check_handle(h);
+    if (nterms < 0 || nterms > kMaxSrc) throw InvalidArg("nterms must be in 0..4");
+    if (nterms > 0 && (!sigma_reim || !S_dev)) throw InvalidArg("sigma_reim / S_dev is NULL");
+    for (int k = 0; k < nterms; ++k) {
+      if (!S_dev[k]) throw InvalidArg("source tensor is NULL");
+      if (!std::isfinite(sigma_reim[2 * k]) || !std::isfinite(sigma_reim[2 * k + 1]))
+        throw InvalidArg("sigma must be finite");
+    }
+    h->eng->set_source(nterms, sigma_reim, S_dev);
+  });
+}
+
+fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta, const void* v, void* out) {
+  return guarded([&] {
+    check_handle(h);
+    if (func < FCGLE_F_INV || func > FCGLE_F_PHI) throw InvalidArg("unknown func");
+    if (func == FCGLE_F_PHI && (k < 0 || k > 4)) throw InvalidArg("phi order k must be in 0..4");
+    if (!std::isfinite(theta)) throw InvalidArg("theta must be finite");
+    if (!v || !out) throw InvalidArg("tensor pointer is NULL");
+    h->eng->apply_f(func, k, theta, v, out);
+  });
+}
+
+fcgle_status fcgle_step(fcgle_handle h, int scheme, double tau, double t, void* u) {
+  return guarded([&] {
+    check_handle(h);
+    check_scheme(scheme);
+    if (scheme == FCGLE_LBDF2) throw InvalidArg("LBDF2 is a two-step scheme: use fcgle_integrate");
+    check_tau(tau);
+    if (!u) throw InvalidArg("u is NULL");
+    h->eng->step(scheme, tau, t, u);
+  });
+}
+
+fcgle_status fcgle_integrate(fcgle_handle h, int scheme, double tau, int nsteps, double t0, const void* u0,
+                             void* uT) {
+  return guarded([&] {
+    check_handle(h);
+    check_scheme(scheme);
+    check_tau(tau);
+    if (nsteps < 0) throw InvalidArg("nsteps must be >= 0");
+    if (!u0 || !uT) throw InvalidArg("tensor pointer is NULL");
+    h->eng->integrate(scheme, tau, nsteps, t0, u0, uT);
+  });
+}
+
+fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int nsteps, double t0,
+                                  const void* u0_host, void* uT_host) {
+  return guarded([&] {
+    check_handle(h);
+    check_scheme(scheme);
+    check_tau(tau);
+    if (nsteps < 0) throw InvalidArg("nsteps must be >= 0");
+    if (!u0_host || !uT_host) throw InvalidArg("tensor pointer is NULL");
+    h->eng->integrate_host(scheme, tau, nsteps, t0, u0_host, uT_host);
+    if (int code = h->eng->device_error())
+      throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
+  });
+}
+
+fcgle_status fcgle_norm(fcgle_handle h, const void* u, double* out_host) {
+  return guarded([&] {
+    check_handle(h);
+    if (!u || !out_host) throw InvalidArg("pointer is NULL");
+    *out_host = h->eng->norm(u);
+  });
+}
+
+fcgle_status fcgle_sync(fcgle_handle h) {
+  return guarded([&] {
+    check_handle(h);
+    if (int code = h->eng->device_error())
+      throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
+  });
+}
+
+fcgle_status fcgle_sizes(fcgle_handle h, size_t* n_elems, size_t* n_bytes) {
+  return guarded([&] {
+    check_handle(h);
+    size_t N = 1;
+    for (int mu = 0; mu < h->prm.d; ++mu) N *= (size_t)h->prm.n[mu];
+    if (n_elems) *n_elems = N;
+    if (n_bytes) *n_bytes = N * h->eng->elem_bytes();
+  });
+}
+
+fcgle_status fcgle_launch_count(fcgle_handle h, long long* count) {
+  return guarded([&] {
+    check_handle(h);
+    if (!count) throw InvalidArg("count is NULL");
+    *count = h->eng->launches;
+  });
+}
+
+fcgle_status fcgle_destroy(fcgle_handle h) {
+  return guarded([&] {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+  });
+}
+
+const char* fcgle_status_string(fcgle_status s) {
+  switch (s) {
+    case FCGLE_OK: return "FCGLE_OK";
+    case FCGLE_ERR_INVALID_ARG: return "FCGLE_ERR_INVALID_ARG";
+    case FCGLE_ERR_NOMEM: return "FCGLE_ERR_NOMEM";
+    case FCGLE_ERR_CUDA: return "FCGLE_ERR_CUDA";
+    case FCGLE_ERR_NUMERIC: return "FCGLE_ERR_NUMERIC";
+    case FCGLE_ERR_TIMEOUT: return "FCGLE_ERR_TIMEOUT";
+    case FCGLE_ERR_UNSUPPORTED: return "FCGLE_ERR_UNSUPPORTED";
+  }
+  return "FCGLE_ERR_UNKNOWN";
+}
+
+const char* fcgle_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

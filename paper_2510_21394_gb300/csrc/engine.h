@@ -1,0 +1,54 @@
+// Host-side engine of one FCGLE handle: spectral setup, buffers and the
+// time-stepping schemes, all enqueued on the handle's stream.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/fcgle.h"
+#include "common.h"
+
+namespace fcgle {
+
+struct InvalidArg : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct Unsupported : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct NumericError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct DeviceTimeout : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+// Per-direction FP64 spectral data, computed once at setup on the host.
+struct Direction {
+  int n = 0, p = 0;
+  double h = 0;
+  std::vector<double> Q;     // n x n row-major, column j = eigenvector j
+  std::vector<double> lam;   // n eigenvalues of D_mu (negative)
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() = default;
+  virtual void set_stream(cudaStream_t st) = 0;
+  virtual void set_source(int nterms, const double* sig, const void* const* S_user) = 0;
+  virtual void apply_f(int func, int k, double theta, const void* v, void* out) = 0;
+  virtual void step(int scheme, double tau, double t, void* u) = 0;
+  virtual void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
+  virtual void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
+  virtual double norm(const void* u) = 0;
+  virtual size_t elem_bytes() const = 0;
+  virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
+  long long launches = 0;
+};
+
+std::unique_ptr<EngineBase> make_engine(const fcgle_params& prm, cudaStream_t st);
+
+}  // namespace fcgle

@@ -1,0 +1,113 @@
+// FP64 mu-mode products (paper Sec. 3.2: "each [mode product] realized in
+// practice with a single BLAS call") in the rotating layout of common.h.
+//
+// GEMM view: C[row][col] = sum_kk A(row, kk) * B[col][kk], written with the
+// output index `col` as the slowest one.
+//   real matrix M (p x p):        row = (c, r), 2R rows; kk = k, K = p;
+//     A(row, k) = X[row * p + k];  Y[c][i][r] = C[(c, r)][i].
+//   complex matrix in real block form B = [[Re E, -Im E], [Im E, Re E]]
+//   (2p x 2p):                    row = r, R rows; kk = (c, k), K = 2p;
+//     A(r, (c, k)) = X[c][r][k];   Y[c'][i][r] = C[r][(c', i)].
+// GB300's FP64 rate is a small fraction of its tensor-core rate, so this
+// is a plain shared-memory tiled SIMT GEMM (64 x 64 tile, 4 x 4 per thread):
+// it is FP64-ALU bound by a wide margin at every size used here.
+#include "common.h"
+
+namespace fcgle {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(NT) mp_f64_kernel(const double* __restrict__ X, double* __restrict__ Y,
+                                                    const double* __restrict__ B, int p, long long R) {
+  __shared__ double As[BK][BM + 2];
+  __shared__ double Bs[BK][BN + 2];
+  const long long rows = CPLX ? R : 2 * R;
+  const int K = CPLX ? 2 * p : p;
+  const int Ncol = CPLX ? 2 * p : p;
+  const long long Rp = R * (long long)p;
+
+  const long long row0 = (long long)blockIdx.x * BM;
+  const int col0 = blockIdx.y * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;   // rows tx*4.., cols ty*4..
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  const int lk = tid & 15, lr = tid >> 4;   // loader: k offset, row offset (+16 j)
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kk = k0 + lk;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long row = row0 + lr + 16 * j;
+      double a = 0.0;
+      if (row < rows && kk < K) {
+        if (CPLX) {
+          const int c = kk >= p ? 1 : 0;
+          a = X[c * Rp + row * p + (kk - c * p)];
+        } else {
+          a = X[row * p + kk];
+        }
+      }
+      As[lk][lr + 16 * j] = a;
+      const int col = col0 + lr + 16 * j;
+      Bs[lk][lr + 16 * j] = (col < Ncol && kk < K) ? B[(long long)col * K + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tx * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int col = col0 + ty * 4 + j;
+    if (col >= Ncol) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long row = row0 + tx * 4 + i;
+      if (row >= rows) continue;
+      long long dst;
+      if (CPLX) {
+        const int c = col >= p ? 1 : 0;
+        dst = c * Rp + (long long)(col - c * p) * R + row;
+      } else {
+        const long long c = row >= R ? 1 : 0;
+        dst = c * Rp + (long long)col * R + (row - c * R);
+      }
+      Y[dst] = acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+void mp_f64(const double* X, double* Y, const double* M, int p, size_t R, bool cplx, cudaStream_t st,
+            long long& nl) {
+  const long long rows = cplx ? (long long)R : 2 * (long long)R;
+  const int ncol = cplx ? 2 * p : p;
+  dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)((ncol + BN - 1) / BN));
+  if (cplx)
+    mp_f64_kernel<true><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+  else
+    mp_f64_kernel<false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+  FCGLE_LAUNCHED(nl);
+}
+
+}  // namespace fcgle

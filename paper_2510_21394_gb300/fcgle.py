@@ -1,0 +1,265 @@
+"""Thin Python binding of the C ABI in include/fcgle.h (argument marshalling only).
+
+Every function of the C ABI is exposed under the same name and takes torch
+tensors (device memory, complex128 for FP64 handles / complex64 for BF16X3
+handles, shape (n_d, ..., n_1) contiguous = vec order with j_1 fastest) or
+plain Python numbers.  All arithmetic happens in libfcgle.so; if the library
+is missing this module raises at import time (there is no fallback).
+
+``Solver`` is a convenience wrapper that owns a handle.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcgle.so")
+
+FCGLE_OK = 0
+FCGLE_ERR_INVALID_ARG = 1
+FCGLE_ERR_NOMEM = 2
+FCGLE_ERR_CUDA = 3
+FCGLE_ERR_NUMERIC = 4
+FCGLE_ERR_TIMEOUT = 5
+FCGLE_ERR_UNSUPPORTED = 6
+
+FCGLE_FP64 = 0
+FCGLE_BF16X3 = 2
+
+FCGLE_F_INV = 0
+FCGLE_F_EXP = 1
+FCGLE_F_PHI = 2
+
+SCHEMES = {"lie": 0, "lawson_euler": 1, "lawson_rk2": 2, "etd2rk": 3, "krogstad": 4, "lbdf2": 5, "strang": 6}
+FUNCS = {"inv": FCGLE_F_INV, "exp": FCGLE_F_EXP, "phi": FCGLE_F_PHI}
+PRECISIONS = {"fp64": FCGLE_FP64, "bf16x3": FCGLE_BF16X3}
+
+# exported symbols of include/fcgle.h (checked by the CPU tests)
+EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f", "fcgle_step",
+           "fcgle_integrate", "fcgle_integrate_host", "fcgle_norm", "fcgle_sync", "fcgle_sizes",
+           "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error"]
+
+
+class fcgle_params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int * 3), ("a", ctypes.c_double * 3),
+                ("b", ctypes.c_double * 3), ("alpha", ctypes.c_double * 3),
+                ("nu", ctypes.c_double), ("eta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("fd_order", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class FcgleError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2510_21394_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sig = {
+        "fcgle_setup": [ctypes.POINTER(fcgle_params), P, ctypes.POINTER(H)],
+        "fcgle_set_stream": [H, P],
+        "fcgle_set_source": [H, I, ctypes.POINTER(D), ctypes.POINTER(P)],
+        "fcgle_apply_f": [H, I, I, D, P, P],
+        "fcgle_step": [H, I, D, D, P],
+        "fcgle_integrate": [H, I, D, I, D, P, P],
+        "fcgle_integrate_host": [H, I, D, I, D, P, P],
+        "fcgle_norm": [H, P, ctypes.POINTER(D)],
+        "fcgle_sync": [H],
+        "fcgle_sizes": [H, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+        "fcgle_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
+        "fcgle_destroy": [H],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fcgle_status_string.argtypes = [ctypes.c_int]
+    lib.fcgle_status_string.restype = ctypes.c_char_p
+    lib.fcgle_last_error.argtypes = []
+    lib.fcgle_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def status_name(s):
+    return _lib.fcgle_status_string(int(s)).decode()
+
+
+def _check(status):
+    if status != FCGLE_OK:
+        raise FcgleError(status, _lib.fcgle_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ C ABI mirror
+def fcgle_setup(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, precision="fp64", stream=None):
+    p = fcgle_params()
+    p.d = len(ns)
+    for mu in range(3):
+        p.n[mu] = int(ns[mu]) if mu < p.d else 1
+        p.a[mu] = float(boxes[mu][0]) if mu < p.d else 0.0
+        p.b[mu] = float(boxes[mu][1]) if mu < p.d else 1.0
+        p.alpha[mu] = float(alphas[mu]) if mu < p.d else 1.5
+    p.nu, p.eta, p.gamma, p.kappa, p.zeta = map(float, (nu, eta, gamma, kappa, zeta))
+    p.fd_order = int(fd_order)
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    h = ctypes.c_void_p()
+    _check(_lib.fcgle_setup(ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fcgle_set_stream(h, stream=None):
+    _check(_lib.fcgle_set_stream(h, _stream(stream)))
+
+
+def fcgle_set_source(h, sigmas, tensors):
+    n = len(sigmas)
+    sig = (ctypes.c_double * max(1, 2 * n))()
+    for k, s in enumerate(sigmas):
+        s = complex(s)
+        sig[2 * k], sig[2 * k + 1] = s.real, s.imag
+    ptrs = (ctypes.c_void_p * max(1, n))(*[t.data_ptr() for t in tensors])
+    _check(_lib.fcgle_set_source(h, n, sig, ptrs))
+
+
+def fcgle_apply_f(h, func, k, theta, v, out):
+    func = FUNCS[func] if isinstance(func, str) else int(func)
+    _check(_lib.fcgle_apply_f(h, func, int(k), float(theta), _ptr(v), _ptr(out)))
+
+
+def fcgle_step(h, scheme, tau, t, u):
+    scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(_lib.fcgle_step(h, scheme, float(tau), float(t), _ptr(u)))
+
+
+def fcgle_integrate(h, scheme, tau, nsteps, t0, u0, uT):
+    scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(_lib.fcgle_integrate(h, scheme, float(tau), int(nsteps), float(t0), _ptr(u0), _ptr(uT)))
+
+
+def fcgle_integrate_host(h, scheme, tau, nsteps, t0, u0, uT):
+    scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(_lib.fcgle_integrate_host(h, scheme, float(tau), int(nsteps), float(t0), _ptr(u0), _ptr(uT)))
+
+
+def fcgle_norm(h, u):
+    out = ctypes.c_double()
+    _check(_lib.fcgle_norm(h, _ptr(u), ctypes.byref(out)))
+    return out.value
+
+
+def fcgle_sync(h):
+    _check(_lib.fcgle_sync(h))
+
+
+def fcgle_sizes(h):
+    n = ctypes.c_size_t()
+    b = ctypes.c_size_t()
+    _check(_lib.fcgle_sizes(h, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
+
+
+def fcgle_launch_count(h):
+    c = ctypes.c_longlong()
+    _check(_lib.fcgle_launch_count(h, ctypes.byref(c)))
+    return c.value
+
+
+def fcgle_destroy(h):
+    _check(_lib.fcgle_destroy(h))
+
+
+def fcgle_status_string(s):
+    return status_name(s)
+
+
+def fcgle_last_error():
+    return _lib.fcgle_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience
+class Solver:
+    """Owns one handle; tensors are torch tensors of shape (n_d, ..., n_1)."""
+
+    def __init__(self, ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, precision="fp64",
+                 stream=None):
+        self.ns = list(ns)
+        self.shape = tuple(reversed(self.ns))
+        self.precision = precision
+        self.dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.h = fcgle_setup(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order, precision, stream)
+        self._src = None
+
+    def close(self):
+        if self.h is not None:
+            fcgle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t):
+        if t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_cuda:
+            raise ValueError(f"expected a CUDA {self.dtype} tensor of shape {self.shape}")
+        return t
+
+    def set_source(self, sigmas, tensors):
+        tensors = [self._check_tensor(t.contiguous()) for t in tensors]
+        fcgle_set_source(self.h, sigmas, tensors)
+
+    def apply_f(self, func, k, theta, v, out=None):
+        v = self._check_tensor(v.contiguous())
+        out = torch.empty_like(v) if out is None else out
+        fcgle_apply_f(self.h, func, k, theta, v, out)
+        return out
+
+    def step(self, scheme, tau, t, u):
+        fcgle_step(self.h, scheme, tau, t, self._check_tensor(u))
+        return u
+
+    def integrate(self, scheme, tau, nsteps, u0, t0=0.0, out=None):
+        u0 = self._check_tensor(u0.contiguous())
+        out = torch.empty_like(u0) if out is None else out
+        fcgle_integrate(self.h, scheme, tau, nsteps, t0, u0, out)
+        return out
+
+    def integrate_host(self, scheme, tau, nsteps, u0_host, out_host, t0=0.0):
+        fcgle_integrate_host(self.h, scheme, tau, nsteps, t0, u0_host, out_host)
+        return out_host
+
+    def norm(self, u):
+        return fcgle_norm(self.h, self._check_tensor(u))
+
+    def sync(self):
+        fcgle_sync(self.h)
+
+    def launches(self):
+        return fcgle_launch_count(self.h)
