@@ -1,0 +1,98 @@
+"""Split-BF16 tensor-core path (complex64 storage) vs the FP64 oracle.
+
+Tolerances follow from the arithmetic: each mode product rounds both
+operands to 16 significant bits (x = x_hi + x_lo, |x - x_hi - x_lo| <= 2^-17 |x|)
+and drops x_lo * M_lo, so one mode product has a relative error of a few
+2^-17 ~ 8e-6 (plus FP32 storage, 6e-8); f(theta K) v chains 2d of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import schemes, tensor
+from paper_2510_21394_gb300 import inputs
+from helpers import PARS, SMALL_CASES, rand_tensor, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_APPLY = 1e-4      # 2d <= 6 split-bf16 mode products
+TOL_INTEGRATE = 1e-4  # a few steps of a scheme at small sizes
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_21394_gb300 import fcgle
+    return fcgle
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(torch.complex64).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def test_identity_roundtrip(fc):
+    # phi_0(0 K) = I: forward then backward Tucker must reproduce v to bf16x3 accuracy
+    ns, boxes, al = SMALL_CASES[4]
+    s = fc.Solver(ns, boxes, al, **PARS, precision="bf16x3")
+    V = rand_tensor(ns, 1).astype(np.complex64).astype(np.complex128)
+    got = _host(s.apply_f("inv", 0, 0.0, _dev(V)))
+    s.sync()
+    assert rel(got, V) <= 3e-5
+
+
+@pytest.mark.parametrize("case", range(len(SMALL_CASES)))
+def test_apply_f_parity(fc, case):
+    ns, boxes, al = SMALL_CASES[case]
+    P = tensor.Problem(ns, boxes, al, *PARS.values())
+    S = tensor.Spectral(P)
+    s = fc.Solver(ns, boxes, al, **PARS, precision="bf16x3")
+    V = rand_tensor(ns, 20 + case)
+    v = _dev(V)
+    V32 = V.astype(np.complex64).astype(np.complex128)
+    for th in (1e-3, 0.07):
+        for func, k in (("inv", 0), ("exp", 0), ("phi", 1), ("phi", 2), ("phi", 3)):
+            ref = S.apply_f(func, k, th, V32)
+            got = _host(s.apply_f(func, k, th, v))
+            assert rel(got, ref) <= TOL_APPLY, (func, k, th, rel(got, ref))
+    s.sync()
+    s.close()
+
+
+@pytest.mark.parametrize("scheme", ["lie", "lawson_euler", "lawson_rk2", "etd2rk", "krogstad", "lbdf2", "strang"])
+def test_integrate_parity(fc, scheme):
+    ns, boxes, al = SMALL_CASES[4]
+    P = tensor.Problem(ns, boxes, al, *PARS.values())
+    u0 = (0.8 * inputs.gaussian_pulse(ns, [(-2.0, 2.0)] * 3) * np.exp(1j * rand_tensor(ns, 4).real))
+    u0 = u0.astype(np.complex64).astype(np.complex128)
+    src = [] if scheme == "strang" else [0.3 * rand_tensor(ns, 5).astype(np.complex64).astype(np.complex128)]
+    sig = [] if scheme == "strang" else [-0.7 + 2.0j]
+    g = schemes.Nonlinearity(P, sig, src)
+    tau, m = 0.013, 7
+    ref = schemes.integrate(tensor.Spectral(P), g, scheme, tau, m, u0, t0=0.2)
+    s = fc.Solver(ns, boxes, al, **PARS, precision="bf16x3")
+    if src:
+        s.set_source(sig, [_dev(x) for x in src])
+    got = _host(s.integrate(scheme, tau, m, _dev(u0), t0=0.2))
+    s.sync()
+    assert rel(got, ref) <= TOL_INTEGRATE, rel(got, ref)
+    s.close()
+
+
+def test_large_mode_sizes(fc):
+    # p > 128 and p > 256 exercise several i-blocks and k-chunks of the kernel
+    for ns in ([300, 9], [20, 257, 6]):
+        boxes = [(-5.0, 5.0)] * len(ns)
+        al = [1.3, 1.6, 1.8][: len(ns)]
+        P = tensor.Problem(ns, boxes, al, *PARS.values())
+        V = rand_tensor(ns, 7).astype(np.complex64).astype(np.complex128)
+        s = fc.Solver(ns, boxes, al, **PARS, precision="bf16x3")
+        got = _host(s.apply_f("phi", 1, 0.01, _dev(V)))
+        s.sync()
+        assert rel(got, tensor.Spectral(P).apply_f("phi", 1, 0.01, V)) <= TOL_APPLY
+        s.close()
