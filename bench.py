@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: 3D FCGLE on a 256^3 grid, Krogstad's exponential RK4 (phi_1..phi_3),
+tau = 1e-3, complex64 storage with split-BF16 tensor-core mode products.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One "step" is one Krogstad time step of the whole hot path (4 forward + 4
+backward 3D Tucker operators = 24 mode products, the nonlinearity, the
+spectral stage combinations) over the 256^3 tensor.  The timed region is one
+fcgle_integrate call of K steps (CUDA events on the handle's stream, inputs
+resident in HBM, every tensor 134 MB > L2).  Prints one JSON line on rank 0.
+
+Multi-GPU: one independent replica per GPU (the single-instance path has no
+data-parallel split without an all-to-all exchange), weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 256
+BOXES = [(-10.0, 10.0)] * 3
+ALPHAS = [1.2, 1.5, 1.8]
+PARS = dict(nu=1.0, eta=0.5, gamma=1.0, kappa=1.0, zeta=0.5)
+TAU = 1e-3
+METRIC = "DoF*steps/s"
+UNIT = "DoF*steps/s"
+
+
+def workload_config(n, precision="bf16x3"):
+    return {
+        "workload": f"3D FCGLE {n}^3 on (-10,10)^3, alpha=(1.2,1.5,1.8), nu=1, eta=0.5, gamma=1, kappa=1, "
+                    f"zeta=0.5; Krogstad exponential RK4 (phi_1..phi_3), tau=1e-3; u0 = Gaussian bump x "
+                    f"smoothed random phase (seed 1)",
+        "grid": [n, n, n],
+        "scheme": "krogstad",
+        "tau": TAU,
+        "precision": precision,
+        "storage": "complex64" if precision == "bf16x3" else "complex128",
+        "l2": "inputs larger than L2 (each 256^3 tensor is 134 MB complex64)",
+        "parallelism": "replicas (one independent instance per GPU)",
+    }
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_sample(n, max_steps, budget_s):
+    """The FP64 oracle (as it stands) on the same workload: setup, then whole
+    Krogstad steps until max_steps or the time budget is used."""
+    import numpy as np
+    from oracle import schemes, tensor
+    from paper_2510_21394_gb300 import inputs
+    ns = [n, n, n]
+    t0 = time.perf_counter()
+    P = tensor.Problem(ns, BOXES, ALPHAS, *PARS.values())
+    S = tensor.Spectral(P)
+    for l in (1, 2):
+        S.F("phi", l, TAU / 2)
+    for l in (1, 2, 3):
+        S.F("phi", l, TAU)
+    setup = time.perf_counter() - t0
+    u = inputs.gaussian_random_phase(ns, BOXES, seed=1)
+    g = schemes.Nonlinearity(P)
+    done, t_run = 0, 0.0
+    while done < max_steps:
+        t1 = time.perf_counter()
+        u = schemes.krogstad_step(S, g, TAU, done * TAU, u)
+        t_run += time.perf_counter() - t1
+        done += 1
+        if t_run > budget_s:
+            break
+    assert np.all(np.isfinite(u))
+    return {"value": n ** 3 * done / t_run, "seconds": t_run, "steps": done, "setup_s": setup,
+            "cores": os.cpu_count()}
+
+
+def run_cpu_sample_subprocess(n, max_steps, budget_s, timeout_s):
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n), str(max_steps), str(budget_s)]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(gpu_index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+        self.t_start = self.t_end = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        import statistics
+        reasons = sorted({self.NAMES[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(n):
+    """DRAM bytes per launch of the mode-product kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", "mp_bf16x3.cu")
+    prof = os.path.join(ROOT, "profiles", "mp_bf16x3_256cube.md")
+    if not os.path.exists(prof):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(prof).read()
+    m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic bytes per launch \(scaled to %d\^3\):\s*([0-9.eE+]+)" % n, text)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# -------------------------------------------------------------- main arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    budget = float(os.environ.get("FCGLE_REF_BUDGET_S", "60"))
+    res = run_cpu_sample_subprocess(N_GRID, max(1, args.steps), budget, timeout_s=1800)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(N_GRID, "fp64-oracle"),
+        "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": f"{res['steps']} whole Krogstad step(s) of the {N_GRID}^3 workload "
+                                   f"(of the {args.steps} requested; time budget {budget:.0f} s), numpy FP64 "
+                                   f"tensor-form oracle, setup ({res['setup_s']:.1f} s) excluded"},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        import __graft_entry__ as g
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2510_21394_gb300 import fcgle, inputs
+
+    n = args.n
+    ns = [n, n, n]
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    solver = fcgle.Solver(ns, BOXES, ALPHAS, **PARS, precision="bf16x3")
+    setup_s = time.perf_counter() - t0
+    u0_np = inputs.gaussian_random_phase(ns, BOXES, seed=1)
+    u0 = torch.from_numpy(u0_np).to(torch.complex64).cuda()
+    out = torch.empty_like(u0)
+
+    # warm-up (also fills the cached phi tensors)
+    solver.integrate("krogstad", TAU, args.warmup, u0, out=out)
+    solver.sync()
+    torch.cuda.synchronize()
+
+    clock = ClockSampler(gpu_index_for(local_rank)) if rank == 0 else None
+    time.sleep(0.3 if clock else 0.0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = solver.launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.integrate("krogstad", TAU, args.steps, u0, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = solver.launches() - l0
+    solver.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clock.stop() if clock else None
+    dof = n ** 3
+    value = world * dof * args.steps / (ms / 1e3)
+
+    # ---- dominant kernel: the split-BF16 mode product, timed alone on the same stream
+    P = fcgle.fcgle_internal_elems(solver.h)
+    X = torch.randn(2 * P, device="cuda", dtype=torch.float32)
+    Y = torch.empty_like(X)
+    for d_ in range(3):
+        fcgle.fcgle_mode_product(solver.h, d_, True, X, Y)
+    torch.cuda.synchronize()
+    reps = 5
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        for d_ in range(3):
+            fcgle.fcgle_mode_product(solver.h, d_, True, X, Y)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    solver.sync()
+    mp_ms = k0.elapsed_time(k1) / (3 * reps)
+    mp_bytes = 2 * (2 * P * 4)       # read X, write Y (FP32)
+    peak, peak_kind = measured_peaks()
+    achieved = mp_bytes / (mp_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(n),
+                "kernel": "mp_bf16x3_kernel (one 256^3 mode product)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
+    del X, Y
+
+    # ---- end to end through the C ABI with host buffers
+    hin = torch.from_numpy(u0_np.astype(np.complex64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    solver.integrate_host("krogstad", TAU, args.steps, hin, hout)
+    e2e_s = time.perf_counter() - t1
+    e2e = {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": hin.numel() * 8 / args.steps, "d2h_bytes_per_step": hout.numel() * 8 / args.steps,
+           "note": "fcgle_integrate_host: one H2D of u0 (pinned) and one D2H of u(T) per call of K steps, "
+                   "synchronised, wall clock"}
+
+    extra = {}
+    if not args.no_fp64 and rank == 0:
+        # ---- the plain FP64 GPU form on the same workload, and the accuracy of BF16x3 against it
+        acc_steps = min(args.steps, args.accuracy_steps)
+        s64 = fcgle.Solver(ns, BOXES, ALPHAS, **PARS, precision="fp64")
+        v64 = torch.from_numpy(u0_np).cuda()
+        o64 = torch.empty_like(v64)
+        s64.integrate("krogstad", TAU, 1, v64, out=o64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.integrate("krogstad", TAU, 2, v64, out=o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / 2
+        s64.integrate("krogstad", TAU, acc_steps, v64, out=o64)
+        solver.integrate("krogstad", TAU, acc_steps, u0, out=out)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm(out.to(torch.complex128) - o64) / torch.linalg.vector_norm(o64))
+        s64.sync()
+        s64.close()
+        extra["fp64_gpu"] = {"value": dof / (ms64 / 1e3), "unit": UNIT, "ms_per_step": round(ms64, 2),
+                             "speedup_of_bf16x3": round((dof * args.steps / (ms / 1e3) / world) / (dof / (ms64 / 1e3)), 1)}
+        extra["accuracy"] = {"steps": acc_steps, "rel_err_vs_fp64_gpu": err,
+                             "note": "FP64 GPU path is parity-tested against the FP64 oracle at <= 1e-12"}
+    solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = run_cpu_sample_subprocess(n, 1, 0.0, timeout_s=900)
+            cpu = {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                   "sample": f"{res['steps']} whole Krogstad step of the {n}^3 workload ({res['seconds']:.1f} s), "
+                             f"numpy FP64 tensor-form oracle on the host cores, setup ({res['setup_s']:.1f} s) excluded"}
+        except Exception as e:  # report, do not fail the GPU measurement
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "setup_s": round(setup_s, 3)}
+        line.update(extra)
+        print(json.dumps(line))
+    return 0
+
+
+def run_mp_only(args):
+    """Raw mode products on internal-layout buffers, for kernel profiling."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_21394_gb300 import fcgle
+    n = args.n
+    s = fcgle.Solver([n] * 3, BOXES, ALPHAS, **PARS, precision=args.precision)
+    P = fcgle.fcgle_internal_elems(s.h)
+    dt = torch.float32 if args.precision == "bf16x3" else torch.float64
+    X = torch.randn(2 * P, device="cuda", dtype=dt)
+    Y = torch.empty_like(X)
+    for _ in range(args.mp_only):
+        for d_ in range(3):
+            fcgle.fcgle_mode_product(s.h, d_, True, X, Y)
+    torch.cuda.synchronize()
+    s.sync()
+    s.close()
+    print(json.dumps({"mp_only": args.mp_only, "n": n, "precision": args.precision, "ok": True}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--accuracy-steps", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", nargs=3, default=None)
+    ap.add_argument("--mp-only", type=int, default=0, metavar="REPS",
+                    help="only run REPS x 3 raw mode products (all directions) of the n^3 workload (profiling)")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    args = ap.parse_args()
+    if args.mp_only:
+        return run_mp_only(args)
+    if args.cpu_sample:
+        n, steps, budget = int(args.cpu_sample[0]), int(args.cpu_sample[1]), float(args.cpu_sample[2])
+        print(json.dumps(cpu_sample(n, steps, budget)))
+        return 0
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -103,6 +103,7 @@ class Spectral:
             shp[P.d - mu] = len(w)
             L = L + w.reshape(shp)
         self.Lam = P.c * L
+        self._F = {}
 
     def fwd(self, V):
         return tucker(V, [Q.T for Q in self.Q])
@@ -111,7 +112,12 @@ class Spectral:
         return tucker(W, self.Q)
 
     def F(self, kind, ell, theta):
-        return scalar_f(kind, ell, theta * self.Lam)
+        """F = f(theta lam_{j_1..j_d}); computed once per (f, theta) like the
+        paper's R_theta and P_{l,theta} tensors (Sec. 4.1)."""
+        key = (kind, ell if kind == "phi" else 0, float(theta))
+        if key not in self._F:
+            self._F[key] = scalar_f(kind, ell, theta * self.Lam)
+        return self._F[key]
 
     def apply_f(self, kind, ell, theta, V):
         """f(theta K) v in the Tucker form (Eq. fKu_diag)."""

@@ -203,6 +203,23 @@ fcgle_status fcgle_sizes(fcgle_handle h, size_t* n_elems, size_t* n_bytes) {
   });
 }
 
+fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P) {
+  return guarded([&] {
+    check_handle(h);
+    if (!P) throw InvalidArg("P is NULL");
+    *P = h->eng->internal_elems();
+  });
+}
+
+fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int forward, const void* X, void* Y) {
+  return guarded([&] {
+    check_handle(h);
+    if (!X || !Y) throw InvalidArg("tensor pointer is NULL");
+    if (X == Y) throw InvalidArg("X and Y must not overlap");
+    h->eng->mode_product(direction, forward != 0, X, Y);
+  });
+}
+
 fcgle_status fcgle_launch_count(fcgle_handle h, long long* count) {
   return guarded([&] {
     check_handle(h);

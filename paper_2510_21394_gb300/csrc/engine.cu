@@ -148,6 +148,11 @@ class Engine : public EngineBase {
   }
 
   void set_stream(cudaStream_t st) override { st_ = st; }
+  size_t internal_elems() const override { return s_.P; }
+  void mode_product(int mu, bool fwd, const void* X, void* Y) override {
+    if (mu < 0 || mu >= s_.d) throw InvalidArg("direction must be in 0..d-1");
+    mp((const T*)X, (T*)Y, mu, fwd);
+  }
   size_t elem_bytes() const override { return 2 * sizeof(T); }
 
   void set_source(int nterms, const double* sig, const void* const* S_user) override {

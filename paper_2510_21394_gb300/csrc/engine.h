@@ -44,6 +44,8 @@ class EngineBase {
   virtual void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
   virtual void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
   virtual double norm(const void* u) = 0;
+  virtual void mode_product(int mu, bool fwd, const void* X, void* Y) = 0;
+  virtual size_t internal_elems() const = 0;
   virtual size_t elem_bytes() const = 0;
   virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
   long long launches = 0;

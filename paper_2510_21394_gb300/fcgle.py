@@ -38,7 +38,8 @@ PRECISIONS = {"fp64": FCGLE_FP64, "bf16x3": FCGLE_BF16X3}
 # exported symbols of include/fcgle.h (checked by the CPU tests)
 EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f", "fcgle_step",
            "fcgle_integrate", "fcgle_integrate_host", "fcgle_norm", "fcgle_sync", "fcgle_sizes",
-           "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error"]
+           "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
+           "fcgle_internal_elems", "fcgle_mode_product"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -76,6 +77,8 @@ def _load():
         "fcgle_sizes": [H, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
         "fcgle_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
         "fcgle_destroy": [H],
+        "fcgle_internal_elems": [H, ctypes.POINTER(ctypes.c_size_t)],
+        "fcgle_mode_product": [H, I, I, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -188,6 +191,17 @@ def fcgle_launch_count(h):
     c = ctypes.c_longlong()
     _check(_lib.fcgle_launch_count(h, ctypes.byref(c)))
     return c.value
+
+
+def fcgle_internal_elems(h):
+    n = ctypes.c_size_t()
+    _check(_lib.fcgle_internal_elems(h, ctypes.byref(n)))
+    return n.value
+
+
+def fcgle_mode_product(h, direction, forward, X, Y):
+    """X, Y: flat device tensors of 2 P reals (float64 / float32) in the internal layout."""
+    _check(_lib.fcgle_mode_product(h, int(direction), int(bool(forward)), _ptr(X), _ptr(Y)))
 
 
 def fcgle_destroy(h):

@@ -14,8 +14,8 @@ Workloads (recipes; sizes as in the paper's 2D/3D experiments):
 * ``sech_pulse_noise``: sech(|x|) e^{0.5 i x_1} + uniform noise of amplitude
   1e-3 in re and im (PCG64, drawn in vec order).
 * ``gaussian_random_phase``: exp(-|x|^2) e^{i pi xi}, xi white noise (PCG64)
-  smoothed by a separable Gaussian filter of standard deviation ``corr``
-  physical units (zero padded), then standardised.
+  smoothed by a Gaussian of standard deviation ``corr`` physical units (zero
+  padded FFT convolution), then standardised.
 * ``polynomial_manufactured``: the paper's Example 1,
   u = e^{-i t} prod_mu (1 - x_mu^2)^4 on (-1,1)^d, with its continuous source.
 """
@@ -30,9 +30,26 @@ def grid(n, a, b):
 
 
 def mesh(ns, boxes):
-    """Coordinates [X_1, ..., X_d], each of shape (n_d, ..., n_1)."""
-    xs = [grid(n, a, b)[0] for n, (a, b) in zip(ns, boxes)]
-    return np.meshgrid(*reversed(xs), indexing="ij")[::-1]
+    """Coordinates [X_1, ..., X_d] as broadcastable arrays: X_mu has extent
+    n_mu on axis d - mu of the tensor shape (n_d, ..., n_1) and 1 elsewhere."""
+    d = len(ns)
+    out = []
+    for mu, (n, (a, b)) in enumerate(zip(ns, boxes)):
+        shp = [1] * d
+        shp[d - 1 - mu] = n
+        out.append(grid(n, a, b)[0].reshape(shp))
+    return out
+
+
+def _shape(ns):
+    return tuple(reversed([int(n) for n in ns]))
+
+
+def _prod(arrs):
+    out = arrs[0]
+    for a in arrs[1:]:
+        out = out * a
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -97,8 +114,8 @@ def gaussian_manufactured(ns, boxes, alphas, nu, eta, gamma, kappa, zeta):
     S_3 = 2 (1+i)(kappa + i zeta) G^3."""
     X = mesh(ns, boxes)
     gs = [np.exp(-Xm ** 2) for Xm in X]
-    G = np.prod(gs, axis=0)
-    lap = np.zeros_like(G)
+    G = np.broadcast_to(_prod(gs), _shape(ns))
+    lap = np.zeros(_shape(ns))
     for mu in range(len(ns)):
         term = riesz_gaussian(X[mu], alphas[mu])
         for o in range(len(ns)):
@@ -114,7 +131,7 @@ def gaussian_manufactured(ns, boxes, alphas, nu, eta, gamma, kappa, zeta):
 
 def gaussian_exact(ns, boxes, t):
     X = mesh(ns, boxes)
-    return (1 + 1j) * math.exp(-t) * np.exp(-sum(Xm ** 2 for Xm in X))
+    return np.broadcast_to((1 + 1j) * math.exp(-t) * _prod([np.exp(-Xm ** 2) for Xm in X]), _shape(ns)).copy()
 
 
 def polynomial_manufactured(ns, alphas, nu, eta, gamma, kappa, zeta):
@@ -124,8 +141,8 @@ def polynomial_manufactured(ns, alphas, nu, eta, gamma, kappa, zeta):
     boxes = [(-1.0, 1.0)] * len(ns)
     X = mesh(ns, boxes)
     ws = [(1.0 - Xm ** 2) ** 4 for Xm in X]
-    W = np.prod(ws, axis=0)
-    lap = np.zeros_like(W)
+    W = np.broadcast_to(_prod(ws), _shape(ns))
+    lap = np.zeros(_shape(ns))
     for mu in range(len(ns)):
         term = riesz_poly(X[mu], alphas[mu])
         for o in range(len(ns)):
@@ -138,13 +155,13 @@ def polynomial_manufactured(ns, alphas, nu, eta, gamma, kappa, zeta):
 
 def polynomial_exact(ns, t):
     X = mesh(ns, [(-1.0, 1.0)] * len(ns))
-    return np.exp(-1j * t) * np.prod([(1.0 - Xm ** 2) ** 4 for Xm in X], axis=0)
+    return np.broadcast_to(np.exp(-1j * t) * _prod([(1.0 - Xm ** 2) ** 4 for Xm in X]), _shape(ns)).copy()
 
 
 def sech_pulse_noise(ns, boxes, seed=0, amp=1e-3, k1=0.5):
     X = mesh(ns, boxes)
     r = np.sqrt(sum(Xm ** 2 for Xm in X))
-    u = (1.0 / np.cosh(r)) * np.exp(1j * k1 * X[0])
+    u = np.broadcast_to((1.0 / np.cosh(r)) * np.exp(1j * k1 * X[0]), _shape(ns))
     rng = np.random.Generator(np.random.PCG64(seed))
     N = u.size
     re = rng.uniform(-amp, amp, N)
@@ -153,14 +170,29 @@ def sech_pulse_noise(ns, boxes, seed=0, amp=1e-3, k1=0.5):
 
 
 def gaussian_random_phase(ns, boxes, seed=1, corr=1.0):
-    from scipy.ndimage import gaussian_filter1d
+    """exp(-|x|^2) e^{i pi xi}: xi = white noise (PCG64, vec order) convolved
+    with a Gaussian of standard deviation ``corr`` (physical units), the noise
+    zero-padded by 4 standard deviations on every side (FFT convolution),
+    then standardised to zero mean and unit variance."""
     X = mesh(ns, boxes)
     rng = np.random.Generator(np.random.PCG64(seed))
-    xi = rng.standard_normal(X[0].shape)
-    for mu, (n, (a, b)) in enumerate(zip(ns, boxes)):
-        h = (b - a) / (n + 1)
-        xi = gaussian_filter1d(xi, sigma=corr / h, axis=len(ns) - 1 - mu,
-                               mode="constant", cval=0.0, truncate=4.0)
+    xi = rng.standard_normal(_shape(ns))
+    shape = xi.shape                       # (n_d, ..., n_1)
+    hs = [(b - a) / (n + 1) for n, (a, b) in zip(ns, boxes)]
+    sig = [corr / h for h in reversed(hs)]  # per axis of `shape`, in grid points
+    pads = [int(math.ceil(4.0 * s)) for s in sig]
+    full = [n + 2 * p for n, p in zip(shape, pads)]
+    buf = np.zeros(full)
+    buf[tuple(slice(p, p + n) for p, n in zip(pads, shape))] = xi
+    H = np.ones([1] * len(full))
+    for ax, (m, s) in enumerate(zip(full, sig)):
+        f = np.fft.rfftfreq(m) if ax == len(full) - 1 else np.fft.fftfreq(m)
+        hk = np.exp(-2.0 * (math.pi * s * f) ** 2)
+        shp = [1] * len(full)
+        shp[ax] = hk.size
+        H = H * hk.reshape(shp)
+    sm = np.fft.irfftn(np.fft.rfftn(buf) * H, s=full)
+    xi = sm[tuple(slice(p, p + n) for p, n in zip(pads, shape))]
     xi = (xi - xi.mean()) / xi.std()
     u = np.exp(-sum(Xm ** 2 for Xm in X)) * np.exp(1j * math.pi * xi)
     return u.astype(np.complex128)
@@ -168,4 +200,4 @@ def gaussian_random_phase(ns, boxes, seed=1, corr=1.0):
 
 def gaussian_pulse(ns, boxes):
     X = mesh(ns, boxes)
-    return np.exp(-sum(Xm ** 2 for Xm in X)).astype(np.complex128)
+    return np.broadcast_to(np.exp(-sum(Xm ** 2 for Xm in X)), _shape(ns)).astype(np.complex128)

@@ -1,0 +1,80 @@
+"""Kernel-level checks of the raw mode product (fcgle_mode_product).
+
+The eigenvectors are those of the library's own eigensolver, so the checks
+use properties that pin them without knowing their order or signs:
+* a unit input e_k gives column k of M = Q^T: the rows of the result are
+  orthonormal eigenvectors, D q = lam q with lam the Rayleigh quotient
+  (D from the oracle's assembly of Eq. Dnalpha);
+* the BF16x3 kernel equals the FP64 kernel on random data to split-bf16
+  accuracy, and the rotating layout puts the new index slowest.
+"""
+import numpy as np
+import pytest
+
+from oracle import fd
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_21394_gb300 import fcgle
+    return fcgle
+
+
+def _solver(fc, ns, prec):
+    boxes = [(-4.0, 4.0), (-3.0, 3.0), (-5.0, 5.0)][: len(ns)]
+    al = [1.3, 1.7, 1.5][: len(ns)]
+    return fc.Solver(ns, boxes, al, 1.0, 0.4, 0.5, 1.0, 0.2, precision=prec), boxes, al
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("bf16x3", 3e-5)])
+def test_unit_vectors_give_eigenvectors(fc, prec, tol):
+    ns = [37, 6, 5]                       # p = (40, 8, 8): pads in every direction
+    s, boxes, al = _solver(fc, ns, prec)
+    p = [(n + 3) // 4 * 4 for n in ns]
+    P = fc.fcgle_internal_elems(s.h)
+    assert P == int(np.prod(p))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    R = P // p[0]
+    # X[c][r][k]: row r = 0 carries e_k for k = 0..n1-1 in successive rows r = k
+    X = torch.zeros(2, R, p[0], dtype=dt, device="cuda")
+    for k in range(ns[0]):
+        X[0, k, k] = 1.0
+    Y = torch.empty_like(X)
+    fc.fcgle_mode_product(s.h, 0, True, X.reshape(-1), Y.reshape(-1))
+    s.sync()
+    Yn = Y.reshape(2, p[0], R).cpu().numpy().astype(np.float64)
+    assert np.all(Yn[1] == 0.0)                       # imaginary plane untouched
+    assert np.all(Yn[0, ns[0]:, :] == 0.0)            # padded output rows stay zero
+    Q = Yn[0, : ns[0], : ns[0]].T                     # Q[k][i] = (Q^T)[i][k]
+    _, h = fd.grid(ns[0], *boxes[0])
+    D = fd.D_matrix(ns[0], al[0], h)
+    assert np.linalg.norm(Q.T @ Q - np.eye(ns[0])) <= tol * 10
+    lam = np.einsum("ki,kl,li->i", Q, D, Q)
+    assert np.linalg.norm(D @ Q - Q * lam) <= tol * 10 * np.linalg.norm(D)
+    s.close()
+
+
+def test_bf16x3_matches_fp64_kernel(fc):
+    ns = [30, 130, 9]                     # p = (32, 132, 12): 2 i-blocks, 3 k-chunks in direction 2
+    s64, _, _ = _solver(fc, ns, "fp64")
+    s32, _, _ = _solver(fc, ns, "bf16x3")
+    P = fc.fcgle_internal_elems(s64.h)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(2 * P, device="cuda", dtype=torch.float64, generator=gen)
+    for mu in range(3):
+        for fwd in (True, False):
+            Y64 = torch.empty_like(X)
+            Y32 = torch.empty(2 * P, device="cuda", dtype=torch.float32)
+            fc.fcgle_mode_product(s64.h, mu, fwd, X, Y64)
+            fc.fcgle_mode_product(s32.h, mu, fwd, X.float(), Y32)
+            s64.sync()
+            s32.sync()
+            err = float(torch.linalg.vector_norm(Y32.double() - Y64) / torch.linalg.vector_norm(Y64))
+            assert err <= 3e-5, (mu, fwd, err)
+    s64.close()
+    s32.close()
