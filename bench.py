@@ -150,7 +150,7 @@ def measured_peaks():
 def ncu_traffic(n):
     """DRAM bytes per launch of the mode-product kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    src = os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", "mp_bf16x3.cu")
+    src = os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", "b3_kernel.cuh")
     prof = os.path.join(ROOT, "profiles", "mp_bf16x3_256cube.md")
     if not os.path.exists(prof):
         return None
@@ -248,10 +248,11 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- dominant kernel: the split-BF16 mode product, timed alone on the same stream
     P = fcgle.fcgle_internal_elems(solver.h)
-    X = torch.randn(2 * P, device="cuda", dtype=torch.float32)
+    X = torch.randn(2 * P, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+    X = torch.cat([X, torch.zeros_like(X)])      # split input: hi planes, lo planes
     Y = torch.empty_like(X)
     for d_ in range(3):
-        fcgle.fcgle_mode_product(solver.h, d_, True, X, Y)
+        fcgle.fcgle_mode_product(solver.h, d_, 3, X, Y)
     torch.cuda.synchronize()
     reps = 5
     k0 = torch.cuda.Event(enable_timing=True)
@@ -259,17 +260,17 @@ def run_ours(args, rank, world, local_rank):
     k0.record(stream)
     for _ in range(reps):
         for d_ in range(3):
-            fcgle.fcgle_mode_product(solver.h, d_, True, X, Y)
+            fcgle.fcgle_mode_product(solver.h, d_, 3, X, Y)
     k1.record(stream)
     torch.cuda.synchronize()
     solver.sync()
     mp_ms = k0.elapsed_time(k1) / (3 * reps)
-    mp_bytes = 2 * (2 * P * 4)       # read X, write Y (FP32)
+    mp_bytes = 2 * (2 * P * 4)       # read X, write Y (hi + lo bf16 = 4 B per real)
     peak, peak_kind = measured_peaks()
     achieved = mp_bytes / (mp_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": ncu_traffic(n),
-                "kernel": "mp_bf16x3_kernel (one 256^3 mode product)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                "kernel": "mp_b3_kernel<EpiStoreSplit> (one 256^3 mode product, split in/out)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
                 "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
     del X, Y
 
@@ -343,12 +344,16 @@ def run_mp_only(args):
     n = args.n
     s = fcgle.Solver([n] * 3, BOXES, ALPHAS, **PARS, precision=args.precision)
     P = fcgle.fcgle_internal_elems(s.h)
-    dt = torch.float32 if args.precision == "bf16x3" else torch.float64
-    X = torch.randn(2 * P, device="cuda", dtype=dt)
+    if args.precision == "bf16x3":
+        X = torch.randn(4 * P, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+        flags = 3                                   # forward, split input and output
+    else:
+        X = torch.randn(2 * P, device="cuda", dtype=torch.float64)
+        flags = 1
     Y = torch.empty_like(X)
     for _ in range(args.mp_only):
         for d_ in range(3):
-            fcgle.fcgle_mode_product(s.h, d_, True, X, Y)
+            fcgle.fcgle_mode_product(s.h, d_, flags, X, Y)
     torch.cuda.synchronize()
     s.sync()
     s.close()

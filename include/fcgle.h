@@ -155,18 +155,21 @@ fcgle_status fcgle_sync(fcgle_handle h);
 fcgle_status fcgle_sizes(fcgle_handle h, size_t* n_elems, size_t* n_bytes);
 
 /* Internal layout size: P = p_1 * ... * p_d, p_mu = n_mu rounded up to a
- * multiple of 4.  An internal tensor is two planes (re, im) of P reals
+ * multiple of 4 (FP64 handles) or 8 (BF16X3 handles).  An internal tensor is two planes (re, im) of P reals
  * (double for FP64 handles, float for BF16X3 handles), each plane in vec
  * order on the padded extents, padding exactly zero. */
 fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P);
 
 /* One raw mu-mode product (Sec. 3.2) on internal-layout device buffers, for
  * kernel-level testing and timing:
- *   Y[c][i][r] = sum_k M[i][k] X[c][r][k],   M = Q_mu^T (forward != 0) or Q_mu,
+ *   Y[c][i][r] = sum_k M[i][k] X[c][r][k],   M = Q_mu^T (flags bit 0 set) or Q_mu,
  * where X is read with direction mu as its fastest index (r = every other
- * index, in order) and Y gets direction mu as its slowest index.  X and Y
- * hold 2 P reals each and must not overlap.  direction in 0..d-1. */
-fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int forward, const void* X, void* Y);
+ * index, in order) and Y gets direction mu as its slowest index.  By default
+ * X and Y hold 2 P reals each (double / float).  flags bit 1 (BF16X3 handles
+ * only): X and Y are in the split form the tensor-core kernel reads and
+ * writes, 4 P bf16 = the hi planes (re, im) followed by the lo planes, each
+ * value being hi + lo.  X and Y must not overlap.  direction in 0..d-1. */
+fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y);
 
 /* Number of kernel launches this handle has issued since setup (all
  * entry points; used to report launch counts). */

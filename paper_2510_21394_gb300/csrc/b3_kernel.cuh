@@ -1,0 +1,309 @@
+// Split-BF16 mu-mode product on the sm_103a tensor cores (tcgen05 + TMEM + TMA)
+// with a fused pointwise epilogue.
+//
+// One launch computes, in the rotating layout of common.h,
+//     acc[c][i][r] = sum_k M[i][k] X[c][r][k]              (Sec. 3.2, one mode product)
+// where every operand arrives pre-split into two bf16 numbers, x = x_hi + x_lo,
+// and the product is M_hi X_hi + M_hi X_lo + M_lo X_hi with FP32 accumulation
+// in tensor memory (the dropped M_lo X_lo term is below 2^-16 relative).
+// The FP32 result is handed, element by element as a complex number
+// (acc[0][i][r], acc[1][i][r]), to an epilogue functor `Epi` that may read
+// other standard-order tensors, evaluate the nonlinearity or the stage
+// combinations of a scheme and write any outputs, split or FP32.
+//
+// GEMM orientation: D[i][col] = sum_k A[i][k] B[col][k] with A = M (MMA M =
+// 128 output indices i per block) and B = 128 data rows: the same 64 indices
+// r0..r0+63 of the real plane (columns 0..63) and of the imaginary plane
+// (columns 64..127), so each epilogue thread sees complete complex values.
+//
+// Warp roles (10 warps, one CTA per SM, persistent over (r-tile, i-block)):
+//   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x 64 x 64)
+//               bf16 chunks, SWIZZLE_128B, straight into the MMA layout.
+//   warp 1      TMEM allocator and single-thread MMA issuer (3 MMAs per k-step).
+//   warps 2-9   epilogue: TMEM -> registers -> smem transpose -> functor on
+//               coalesced (i, r) runs.  Warp w reads TMEM lane quarter w % 4 and
+//               column groups (w - 2) / 4 and (w - 2) / 4 + 2.
+// Pipelines: 3 smem stages (64 KB each), 2 TMEM accumulators (2 x 128 columns).
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
+// records an error code in *err, drains its own TMA and MMA work, frees its
+// TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.h"
+
+namespace fcgle {
+namespace b3 {
+
+constexpr int BM = 128;     // output indices i per MMA
+constexpr int BR = 64;      // r indices per tile (x 2 planes = MMA N)
+constexpr int BN = 2 * BR;  // MMA N
+constexpr int BK = 64;      // k per chunk (one 128-byte bf16 row)
+constexpr int NSTAGE = 3;
+constexpr int NEPI = 8;     // epilogue warps
+constexpr int NTHREADS = 32 * (2 + NEPI);
+
+constexpr uint32_t kStage = 65536;   // M_hi 16K | M_lo 16K | X_hi 16K | X_lo 16K
+constexpr uint32_t kOffEpi = NSTAGE * kStage;
+constexpr uint32_t kEpiWarp = 32 * 33 * 4;
+constexpr uint32_t kOffBar = kOffEpi + NEPI * kEpiWarp;
+constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;   // + barriers + alignment slack
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
+
+struct KParams {
+  long long R;      // rows per plane of X; row length of the output planes
+  int p;            // extent of the contracted / produced index (rows of M)
+  int m_blocks;     // ceil(p / 128)
+  int k_chunks;     // ceil(p / 64)
+  long long tiles;  // ceil(R / 64)
+  int* err;
+};
+
+// -------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and raises the CTA abort flag) on timeout or,
+// unless `drain` is set, as soon as another role has aborted.  Drain waits
+// (for this CTA's own TMA / MMA work before exit) only stop at the time limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code, bool drain = false) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (!drain && *abort_flag) return false;
+      if (now_ns() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  // K-major, SWIZZLE_128B: rows of 128 bytes, 8-row groups 1024 bytes apart.
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ kernel
+template <class Epi>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
+                 const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
+                 const KParams kp, const Epi epi) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
+  auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty_bar = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
+  auto acc_full = [&](int a) { return smem_u32(&bars[2 * NSTAGE + a]); };
+  auto acc_empty = [&](int a) { return smem_u32(&bars[2 * NSTAGE + 2 + a]); };
+  const uint32_t fin_bar = smem_u32(&bars[2 * NSTAGE + 4]);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kOffBar + 136);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(acc_full(a), 1);
+      mbar_init(acc_empty(a), NEPI);
+    }
+    mbar_init(fin_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const long long units = kp.tiles * kp.m_blocks;
+  const int KC = kp.k_chunks;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const long long tile = u / kp.m_blocks;
+        const int mb = (int)(u % kp.m_blocks);
+        const int r0 = (int)(tile * BR);
+        const int r1 = (int)(kp.R + tile * BR);   // same r in the imaginary plane
+        for (int kc = 0; kc < KC; ++kc, ++g) {
+          const int s = (int)(g % NSTAGE);
+          const uint32_t ph = (g / NSTAGE) & 1;
+          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, kp.err, 1)) { ok = false; break; }
+          const uint32_t st = sbase + s * kStage;
+          mbar_arrive_tx(full_bar(s), kStage);
+          tma_load_2d(st, &tm_mhi, kc * BK, mb * BM, full_bar(s));
+          tma_load_2d(st + 16384, &tm_mlo, kc * BK, mb * BM, full_bar(s));
+          tma_load_2d(st + 32768, &tm_xhi, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 32768 + 8192, &tm_xhi, kc * BK, r1, full_bar(s));
+          tma_load_2d(st + 49152, &tm_xlo, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 49152 + 8192, &tm_xlo, kc * BK, r1, full_bar(s));
+        }
+      }
+      // drain: every issued stage must have landed before the CTA may exit
+      const uint32_t issued = g;
+      for (uint32_t q = issued >= NSTAGE ? issued - NSTAGE : 0; q < issued; ++q)
+        mbar_wait(full_bar(q % NSTAGE), (q / NSTAGE) & 1, abort_flag, kp.err, 7, true);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                 ((uint32_t)(BM >> 4) << 24);
+      uint32_t g = 0, t = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
+        const int a = t & 1;
+        if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, kp.err, 2)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + a * BN;
+        for (int kc = 0; kc < KC; ++kc, ++g) {
+          const int s = (int)(g % NSTAGE);
+          const uint32_t ph = (g / NSTAGE) & 1;
+          if (!mbar_wait(full_bar(s), ph, abort_flag, kp.err, 3)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t ahi = sbase + s * kStage, alo = ahi + 16384;
+          const uint32_t bhi = ahi + 32768, blo = ahi + 49152;
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ++ks) {
+            const uint32_t off = ks * 32;
+            const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
+            mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
+            mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+          }
+          mma_commit(empty_bar(s));
+        }
+        if (!ok) break;
+        mma_commit(acc_full(a));
+      }
+      // drain: all issued MMAs complete before TMEM is released
+      mma_commit(fin_bar);
+      mbar_wait(fin_bar, 0, abort_flag, kp.err, 8, true);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;            // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // which two of the four 16-column groups
+    float* stg = reinterpret_cast<float*>(smem + kOffEpi + (warp - 2) * kEpiWarp);
+    const int rr = lane & 15, hrow = (lane >> 4) * 16;
+    uint32_t t = 0;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x, ++t) {
+      const int a = t & 1;
+      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, kp.err, 9)) break;
+      tc_fence_after();
+      const long long tile = u / kp.m_blocks;
+      const int mb = (int)(u % kp.m_blocks);
+      const int i_base = mb * BM + q * 32;
+#pragma unroll 1
+      for (int g2 = 0; g2 < 2; ++g2) {
+        const int cc = half + 2 * g2;   // 16-column group: r = r0 + 16 cc + 0..15
+        uint32_t vr[16], vi[16];
+        const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
+        tmem_ld16(tl, vr);
+        tmem_ld16(tl + BR, vi);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          stg[lane * 33 + j] = __uint_as_float(vr[j]);
+          stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
+        }
+        __syncwarp();
+        const long long r = tile * BR + cc * 16 + rr;
+#pragma unroll 2
+        for (int it = 0; it < 16; ++it) {
+          const int ii = it + hrow;
+          const int i = i_base + ii;
+          if (i < kp.p && r < kp.R) epi((long long)i * kp.R + r, i, r, stg[ii * 33 + rr], stg[ii * 33 + 16 + rr]);
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(a));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * BN));
+}
+
+}  // namespace b3
+}  // namespace fcgle

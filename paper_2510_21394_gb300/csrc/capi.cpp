@@ -211,12 +211,12 @@ fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P) {
   });
 }
 
-fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int forward, const void* X, void* Y) {
+fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y) {
   return guarded([&] {
     check_handle(h);
     if (!X || !Y) throw InvalidArg("tensor pointer is NULL");
     if (X == Y) throw InvalidArg("X and Y must not overlap");
-    h->eng->mode_product(direction, forward != 0, X, Y);
+    h->eng->mode_product_flags(direction, flags & 3, X, Y);
   });
 }
 

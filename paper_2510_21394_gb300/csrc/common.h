@@ -120,21 +120,6 @@ void sumsq(const Shape& s, const T* X, double* out_dev, cudaStream_t st, long lo
 void mp_f64(const double* X, double* Y, const double* M, int p, size_t R, bool cplx,
             cudaStream_t st, long long& nl);
 
-// BF16x3 on tcgen05, real matrix given as bf16 hi/lo planes.
-struct Bf16x3Op {
-  void* hi = nullptr;     // M_pad x K_pad bf16, zero padded
-  void* lo = nullptr;
-  int p = 0;              // logical size of M (p x p)
-  int m_pad = 0, k_pad = 0;
-  alignas(64) unsigned char tmap_hi[128];
-  alignas(64) unsigned char tmap_lo[128];
-};
-void bf16x3_prepare(const double* M_host, int p, Bf16x3Op& op);   // uploads + tensor maps
-void bf16x3_release(Bf16x3Op& op);
-void mp_bf16x3(const float* X, float* Y, const Bf16x3Op& op, size_t R, int* err_dev,
-               cudaStream_t st, long long& nl);
-int bf16x3_num_sms();
-
 // ------------------------------------------------------------ host setup
 // FP64 symmetric eigendecomposition A = Z diag(w) Z^T (A row-major n x n).
 // Z row-major, column j = eigenvector of w[j]; w ascending.  Returns false if

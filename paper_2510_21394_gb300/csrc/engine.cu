@@ -44,6 +44,31 @@ std::vector<double> build_D(int n, double alpha, double h, int order) {
   return D;
 }
 
+void check_eig(const std::vector<double>& A, const Direction& D) {
+  const int n = D.n;
+  double r = 0, a = 0, o = 0;
+  // residual ||A Q - Q Lam||_F / ||A||_F and ||Q^T Q - I||_F, sampled on up to 64 columns
+  const int stride = n > 64 ? n / 64 : 1;
+  for (int j = 0; j < n; j += stride) {
+    for (int i = 0; i < n; ++i) {
+      double s = 0;
+      for (int k = 0; k < n; ++k) s += A[(size_t)i * n + k] * D.Q[(size_t)k * n + j];
+      s -= D.Q[(size_t)i * n + j] * D.lam[j];
+      r += s * s;
+    }
+    for (int i = 0; i < n; ++i) {
+      double s = 0;
+      for (int k = 0; k < n; ++k) s += D.Q[(size_t)k * n + i] * D.Q[(size_t)k * n + j];
+      if (i == j) s -= 1.0;
+      o += s * s;
+    }
+  }
+  for (size_t i = 0; i < A.size(); ++i) a += A[i] * A[i];
+  const double frac = (double)((n + stride - 1) / stride) / n;
+  if (!(std::sqrt(r / (a * frac)) <= 1e-11) || !(std::sqrt(o / frac) <= 1e-11 * std::sqrt((double)n)))
+    throw NumericError("eigendecomposition residual above 1e-11");
+}
+
 uint64_t dbits(double x) {
   uint64_t u;
   std::memcpy(&u, &x, 8);
@@ -81,24 +106,17 @@ class Engine : public EngineBase {
     }
     // ---- per-direction spectral data (shared between identical directions)
     for (int mu = 0; mu < prm.d; ++mu) {
-      Direction& D = dir_[mu];
-      D.n = prm.n[mu];
-      D.p = s_.p[mu];
-      D.h = (prm.b[mu] - prm.a[mu]) / (prm.n[mu] + 1);
       int same = -1;
+      const double h = (prm.b[mu] - prm.a[mu]) / (prm.n[mu] + 1);
       for (int o = 0; o < mu; ++o)
-        if (prm.n[o] == prm.n[mu] && prm.alpha[o] == prm.alpha[mu] && dir_[o].h == D.h) same = o;
+        if (prm.n[o] == prm.n[mu] && prm.alpha[o] == prm.alpha[mu] && dir_[o].h == h) same = o;
       if (same >= 0) {
-        D.Q = dir_[same].Q;
-        D.lam = dir_[same].lam;
-        continue;
+        dir_[mu] = dir_[same];
+        dir_[mu].p = s_.p[mu];
+      } else {
+        dir_[mu] = spectral_direction(prm, mu);
+        dir_[mu].p = s_.p[mu];
       }
-      std::vector<double> A = build_D(D.n, prm.alpha[mu], D.h, prm.fd_order);
-      D.Q.resize((size_t)D.n * D.n);
-      D.lam.resize(D.n);
-      if (!sym_eig(D.n, A.data(), D.lam.data(), D.Q.data()))
-        throw NumericError("eigendecomposition did not converge");
-      check_eig(A, D);
     }
     // ---- device copies: lam_mu (padded), mode-product matrices
     for (int mu = 0; mu < prm.d; ++mu) {
@@ -114,15 +132,10 @@ class Engine : public EngineBase {
           Mf[(size_t)i * D.p + k] = D.Q[(size_t)k * D.n + i];
           Mb[(size_t)i * D.p + k] = D.Q[(size_t)i * D.n + k];
         }
-      if (kF64) {
-        mf64_[mu][0].reset(new DevBuf<double>(Mf.size()));
-        mf64_[mu][1].reset(new DevBuf<double>(Mb.size()));
-        FCGLE_CUDA(cudaMemcpy(mf64_[mu][0]->ptr, Mf.data(), Mf.size() * 8, cudaMemcpyHostToDevice));
-        FCGLE_CUDA(cudaMemcpy(mf64_[mu][1]->ptr, Mb.data(), Mb.size() * 8, cudaMemcpyHostToDevice));
-      } else {
-        bf16x3_prepare(Mf.data(), D.p, mb3_[mu][0]);
-        bf16x3_prepare(Mb.data(), D.p, mb3_[mu][1]);
-      }
+      mf64_[mu][0].reset(new DevBuf<double>(Mf.size()));
+      mf64_[mu][1].reset(new DevBuf<double>(Mb.size()));
+      FCGLE_CUDA(cudaMemcpy(mf64_[mu][0]->ptr, Mf.data(), Mf.size() * 8, cudaMemcpyHostToDevice));
+      FCGLE_CUDA(cudaMemcpy(mf64_[mu][1]->ptr, Mb.data(), Mb.size() * 8, cudaMemcpyHostToDevice));
     }
     lv_.c_re = prm.nu;
     lv_.c_im = prm.eta;
@@ -141,11 +154,6 @@ class Engine : public EngineBase {
     FCGLE_CUDA(cudaStreamSynchronize(st_));
   }
 
-  ~Engine() override {
-    if (!kF64)
-      for (int mu = 0; mu < kMaxDim; ++mu)
-        for (int f = 0; f < 2; ++f) bf16x3_release(mb3_[mu][f]);
-  }
 
   void set_stream(cudaStream_t st) override { st_ = st; }
   size_t internal_elems() const override { return s_.P; }
@@ -238,39 +246,10 @@ class Engine : public EngineBase {
 
   static bool needs_uhat(int scheme) { return scheme == FCGLE_ETD2RK || scheme == FCGLE_KROGSTAD; }
 
-  void check_eig(const std::vector<double>& A, const Direction& D) {
-    const int n = D.n;
-    double r = 0, a = 0, o = 0;
-    // residual ||A Q - Q Lam||_F / ||A||_F and ||Q^T Q - I||_F, sampled on up to 64 columns
-    const int stride = n > 64 ? n / 64 : 1;
-    for (int j = 0; j < n; j += stride) {
-      for (int i = 0; i < n; ++i) {
-        double s = 0;
-        for (int k = 0; k < n; ++k) s += A[(size_t)i * n + k] * D.Q[(size_t)k * n + j];
-        s -= D.Q[(size_t)i * n + j] * D.lam[j];
-        r += s * s;
-      }
-      for (int i = 0; i < n; ++i) {
-        double s = 0;
-        for (int k = 0; k < n; ++k) s += D.Q[(size_t)k * n + i] * D.Q[(size_t)k * n + j];
-        if (i == j) s -= 1.0;
-        o += s * s;
-      }
-    }
-    for (size_t i = 0; i < A.size(); ++i) a += A[i] * A[i];
-    const double frac = (double)((n + stride - 1) / stride) / n;
-    if (!(std::sqrt(r / (a * frac)) <= 1e-11) || !(std::sqrt(o / frac) <= 1e-11 * std::sqrt((double)n)))
-      throw NumericError("eigendecomposition residual above 1e-11");
-  }
-
   // ---- building blocks
   void mp(const T* X, T* Y, int mu, bool fwd) {
     const size_t R = s_.P / s_.p[mu];
-    if constexpr (kF64) {
-      mp_f64(X, Y, mf64_[mu][fwd ? 0 : 1]->ptr, s_.p[mu], R, false, st_, launches);
-    } else {
-      mp_bf16x3(X, Y, mb3_[mu][fwd ? 0 : 1], R, err_->ptr, st_, launches);
-    }
+    mp_f64(X, Y, mf64_[mu][fwd ? 0 : 1]->ptr, s_.p[mu], R, false, st_, launches);
   }
 
   // Tucker operator over directions 1..d in the rotating order; Y may equal X.
@@ -586,7 +565,6 @@ class Engine : public EngineBase {
   Direction dir_[kMaxDim];
   std::unique_ptr<DevBuf<double>> lam_[kMaxDim];
   std::unique_ptr<DevBuf<double>> mf64_[kMaxDim][2];
-  Bf16x3Op mb3_[kMaxDim][2];
   LamVecs lv_{};
   GParams gp_{};
   std::unique_ptr<DevBuf<T>> buf_[kNumBuf];
@@ -598,9 +576,22 @@ class Engine : public EngineBase {
   std::map<uint64_t, std::vector<std::unique_ptr<DevBuf<double>>>> ecache_;
 };
 
+Direction spectral_direction(const fcgle_params& prm, int mu) {
+  Direction D;
+  D.n = prm.n[mu];
+  D.p = D.n;
+  D.h = (prm.b[mu] - prm.a[mu]) / (prm.n[mu] + 1);
+  std::vector<double> A = build_D(D.n, prm.alpha[mu], D.h, prm.fd_order);
+  D.Q.resize((size_t)D.n * D.n);
+  D.lam.resize(D.n);
+  if (!sym_eig(D.n, A.data(), D.lam.data(), D.Q.data())) throw NumericError("eigendecomposition did not converge");
+  check_eig(A, D);
+  return D;
+}
+
 std::unique_ptr<EngineBase> make_engine(const fcgle_params& prm, cudaStream_t st) {
   if (prm.precision == FCGLE_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(prm, st));
-  if (prm.precision == FCGLE_BF16X3) return std::unique_ptr<EngineBase>(new Engine<float>(prm, st));
+  if (prm.precision == FCGLE_BF16X3) return make_engine_b3(prm, st);
   throw InvalidArg("unknown precision");
 }
 

@@ -45,12 +45,22 @@ class EngineBase {
   virtual void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
   virtual double norm(const void* u) = 0;
   virtual void mode_product(int mu, bool fwd, const void* X, void* Y) = 0;
+  // flags: bit 0 forward (Q^T), bit 1 split-bf16 input and output (BF16X3 only)
+  virtual void mode_product_flags(int mu, int flags, const void* X, void* Y) {
+    if (flags & 2) throw InvalidArg("split input/output needs a BF16X3 handle");
+    mode_product(mu, flags & 1, X, Y);
+  }
   virtual size_t internal_elems() const = 0;
   virtual size_t elem_bytes() const = 0;
   virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
   long long launches = 0;
 };
 
+// D_mu of direction mu (Eq. Dnalpha / Eq. FD4) and its FP64 eigendecomposition
+// (Eq. diag), residual-checked.
+Direction spectral_direction(const fcgle_params& prm, int mu);
+
 std::unique_ptr<EngineBase> make_engine(const fcgle_params& prm, cudaStream_t st);
+std::unique_ptr<EngineBase> make_engine_b3(const fcgle_params& prm, cudaStream_t st);
 
 }  // namespace fcgle

@@ -1,0 +1,578 @@
+// Split-BF16 engine (FCGLE_BF16X3 handles): complex64 storage, tensor-core
+// mode products with fused pointwise epilogues.
+//
+// Storage.  FP32 planar tensors (common.h layout) for everything pointwise
+// code reads (u_n, U^_n, F^_n, D^_2, D^_3, the phi tensors, sources); split
+// tensors (two bf16 arrays hi, lo, each 2 P elements) for everything a mode
+// product reads.  Splitting x = hi + lo at write time loses nothing: the
+// mode product consumes exactly hi and lo.
+//
+// Each time step is a chain of Tucker operators (Eq. fKu_diag); the last mode
+// product of every Tucker operator carries the scheme's pointwise work in its
+// epilogue (b3_epilogues.cuh) and writes the split input of the next Tucker
+// operator, so no standalone pointwise pass runs inside the time loop.
+// Per Krogstad step (Eq. krogstad-m, F^_n = Lam o U^_n + G^_n with U^_n
+// carried): 4 forward + 4 backward Tucker operators = 24 launches for d = 3.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "b3_epilogues.cuh"
+#include "b3_kernel.cuh"
+#include "engine.h"
+
+namespace fcgle {
+
+using b3::SplitOut;
+
+namespace {
+
+template <typename T>
+struct DevMem {
+  T* ptr = nullptr;
+  DevMem() = default;
+  explicit DevMem(size_t n) { FCGLE_CUDA(cudaMalloc(&ptr, n * sizeof(T))); }
+  ~DevMem() {
+    if (ptr) cudaFree(ptr);
+  }
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+};
+
+uint64_t bits_of(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  return u;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    FCGLE_CUDA(cudaGetDevice(&dev));
+    FCGLE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return sms;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    FCGLE_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw std::runtime_error("cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D bf16 tensor map, SWIZZLE_128B, box (64 inner, box_rows outer).
+void encode_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)b3::BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+// ------------------------------------------------------ standalone kernels
+// V = a u + b g(t, u) (split); optionally V2 = a2 u + b2 g(t, u) (split)
+__global__ void gsplit_kernel(long long P, b3::GStatic g, b3::GTime t, const float* __restrict__ U, float a, float b,
+                              SplitOut V, float a2, float b2, SplitOut V2) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P; q += (long long)gridDim.x * blockDim.x) {
+    const float ur = U[q], ui = U[P + q];
+    float gr = 0.f, gi = 0.f;
+    if (b != 0.f || (V2.hi && b2 != 0.f)) b3::g_eval(g, t, P, q, ur, ui, gr, gi);
+    b3::put_csplit(V, P, q, a * ur + b * gr, a * ui + b * gi);
+    if (V2.hi) b3::put_csplit(V2, P, q, a2 * ur + b2 * gr, a2 * ui + b2 * gi);
+  }
+}
+
+// V = Phi_t(u) (split)
+__global__ void flow_split_kernel(long long P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P; q += (long long)gridDim.x * blockDim.x) {
+    float vr, vi;
+    b3::flow_eval(f, U[q], U[P + q], vr, vi);
+    b3::put_csplit(V, P, q, vr, vi);
+  }
+}
+
+// split <-> FP32 (raw mode-product entry point)
+__global__ void to_split_kernel(long long n, const float* __restrict__ X, SplitOut Y) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    b3::put_split(Y, q, X[q]);
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  const long long cap = (long long)num_sms() * 16;
+  return (int)std::max<long long>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+// =========================================================== the engine
+class EngineB3 : public EngineBase {
+ public:
+  EngineB3(const fcgle_params& prm, cudaStream_t st) : prm_(prm), st_(st) {
+    s_.d = prm.d;
+    s_.P = 1;
+    s_.N = 1;
+    for (int mu = 0; mu < kMaxDim; ++mu) {
+      s_.n[mu] = mu < prm.d ? prm.n[mu] : 1;
+      s_.p[mu] = mu < prm.d ? ((prm.n[mu] + 7) & ~7) : 1;   // 16-byte bf16 rows
+      s_.P *= (size_t)s_.p[mu];
+      s_.N *= (size_t)s_.n[mu];
+    }
+    P_ = (long long)s_.P;
+    for (int mu = 0; mu < prm.d; ++mu) {
+      Direction D = spectral_direction(prm, mu);
+      h_[mu] = D.h;
+      std::vector<double> lp(s_.p[mu], 0.0);
+      std::vector<float> lf(s_.p[mu], 0.f);
+      for (int j = 0; j < D.n; ++j) {
+        lp[j] = D.lam[j];
+        lf[j] = (float)D.lam[j];
+      }
+      lam_[mu].reset(new DevMem<double>(s_.p[mu]));
+      lamf_[mu].reset(new DevMem<float>(s_.p[mu]));
+      FCGLE_CUDA(cudaMemcpy(lam_[mu]->ptr, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice));
+      FCGLE_CUDA(cudaMemcpy(lamf_[mu]->ptr, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+      const int p = s_.p[mu];
+      std::vector<double> Mf((size_t)p * p, 0.0), Mb((size_t)p * p, 0.0);
+      for (int i = 0; i < D.n; ++i)
+        for (int k = 0; k < D.n; ++k) {
+          Mf[(size_t)i * p + k] = D.Q[(size_t)k * D.n + i];   // Q^T
+          Mb[(size_t)i * p + k] = D.Q[(size_t)i * D.n + k];   // Q
+        }
+      prepare_matrix(Mf.data(), p, mat_[mu][0]);
+      prepare_matrix(Mb.data(), p, mat_[mu][1]);
+    }
+    lv_.c_re = prm.nu;
+    lv_.c_im = prm.eta;
+    for (int mu = 0; mu < kMaxDim; ++mu) lv_.lam[mu] = mu < prm.d ? lam_[mu]->ptr : nullptr;
+    lf_.d = prm.d;
+    lf_.c_re = (float)prm.nu;
+    lf_.c_im = (float)prm.eta;
+    for (int mu = 0; mu < kMaxDim; ++mu) {
+      lf_.lam[mu] = mu < prm.d ? lamf_[mu]->ptr : nullptr;
+      lf_.p[mu] = s_.p[mu];
+    }
+    gs_.gamma = (float)prm.gamma;
+    gs_.kappa = (float)prm.kappa;
+    gs_.zeta = (float)prm.zeta;
+    gs_.nsrc = 0;
+    for (int i = 0; i < kNumF32; ++i) {
+      f32_[i].reset(new DevMem<float>(2 * s_.P));
+      FCGLE_CUDA(cudaMemsetAsync(f32_[i]->ptr, 0, 2 * s_.P * 4, st_));
+    }
+    for (int i = 0; i < kNumSplit; ++i) {
+      sp_[i].reset(new DevMem<__nv_bfloat16>(4 * s_.P));
+      FCGLE_CUDA(cudaMemsetAsync(sp_[i]->ptr, 0, 4 * s_.P * 2, st_));
+    }
+    scratch_.reset(new DevMem<double>(4));
+    err_.reset(new DevMem<int>(1));
+    FCGLE_CUDA(cudaMemsetAsync(err_->ptr, 0, sizeof(int), st_));
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+    static bool attrs = false;
+    if (!attrs) {
+      set_smem_attr<b3::EpiStoreSplit>();
+      set_smem_attr<b3::EpiStoreF32>();
+      set_smem_attr<b3::EpiScaleSplit>();
+      set_smem_attr<b3::EpiUpdateG>();
+      set_smem_attr<b3::EpiStageD>();
+      set_smem_attr<b3::EpiFhat>();
+      set_smem_attr<b3::EpiStage2>();
+      set_smem_attr<b3::EpiKrogFinal>();
+      set_smem_attr<b3::EpiLBDF2>();
+      set_smem_attr<b3::EpiLawsonRK2>();
+      set_smem_attr<b3::EpiStrang>();
+      attrs = true;
+    }
+  }
+
+  ~EngineB3() override {
+    for (int mu = 0; mu < kMaxDim; ++mu)
+      for (int f = 0; f < 2; ++f) {
+        if (mat_[mu][f].hi) cudaFree(mat_[mu][f].hi);
+        if (mat_[mu][f].lo) cudaFree(mat_[mu][f].lo);
+      }
+  }
+
+  void set_stream(cudaStream_t st) override { st_ = st; }
+  size_t internal_elems() const override { return s_.P; }
+  size_t elem_bytes() const override { return 8; }
+
+  void set_source(int nterms, const double* sig, const void* const* S_user) override {
+    for (int k = 0; k < nterms; ++k) {
+      if (!src_[k]) src_[k].reset(new DevMem<float>(2 * s_.P));
+      pack_f32((const float*)S_user[k], src_[k]->ptr);
+      sig_re_[k] = sig[2 * k];
+      sig_im_[k] = sig[2 * k + 1];
+      gs_.S[k] = src_[k]->ptr;
+    }
+    for (int k = nterms; k < kMaxSrc; ++k) gs_.S[k] = nullptr;
+    gs_.nsrc = nterms;
+  }
+
+  int device_error() override {
+    int h = 0;
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+    FCGLE_CUDA(cudaMemcpy(&h, err_->ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) FCGLE_CUDA(cudaMemset(err_->ptr, 0, sizeof(int)));
+    return h;
+  }
+
+  // raw mode product: flags bit 0 = forward (Q^T), bit 1 = split input and output
+  void mode_product(int mu, bool fwd, const void* X, void* Y) override { mode_product_flags(mu, fwd ? 1 : 0, X, Y); }
+  void mode_product_flags(int mu, int flags, const void* X, void* Y) override {
+    if (mu < 0 || mu >= s_.d) throw InvalidArg("direction must be in 0..d-1");
+    const bool fwd = flags & 1;
+    if (flags & 2) {
+      const __nv_bfloat16* xh = (const __nv_bfloat16*)X;
+      __nv_bfloat16* yh = (__nv_bfloat16*)Y;
+      SplitOut out{yh, yh + 2 * s_.P};
+      launch_mp(xh, xh + 2 * s_.P, mu, fwd, b3::EpiStoreSplit{P_, out});
+    } else {
+      SplitOut t = SP(kT0);
+      to_split_kernel<<<grid_for(2 * P_), 256, 0, st_>>>(2 * P_, (const float*)X, t);
+      FCGLE_LAUNCHED(launches);
+      launch_mp(t.hi, t.lo, mu, fwd, b3::EpiStoreF32{P_, (float*)Y});
+    }
+  }
+
+  // ------------------------------------------------------------ apply_f
+  void apply_f(int func, int k, double theta, const void* v, void* out) override {
+    if (func == FCGLE_F_PHI && k == 0) func = FCGLE_F_EXP;
+    float* X = F32(kWork);
+    pack_f32((const float*)v, X);
+    SplitOut V = SP(kV);
+    gsplit(X, 0.0, 1.f, 0.f, V);
+    const float* Fp = Ften(func, k, theta);
+    tucker(V, true, b3::EpiScaleSplit{P_, Fp, V});
+    tucker(V, false, b3::EpiStoreF32{P_, X});
+    unpack_f32(X, (float*)out);
+  }
+
+  // ---------------------------------------------------------- schemes
+  void step(int scheme, double tau, double t, void* u) override {
+    pack_f32((const float*)u, F32(kU));
+    run(scheme, tau, 1, t);
+    unpack_f32(F32(kU), (float*)u);
+  }
+
+  void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
+    pack_f32((const float*)u0, F32(kU));
+    run(scheme, tau, nsteps, t0);
+    unpack_f32(F32(kU), (float*)uT);
+  }
+
+  void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
+    const size_t bytes = s_.N * 8;
+    if (!host_stage_) host_stage_.reset(new DevMem<float>(2 * s_.N));
+    FCGLE_CUDA(cudaMemcpyAsync(host_stage_->ptr, u0, bytes, cudaMemcpyHostToDevice, st_));
+    pack_f32(host_stage_->ptr, F32(kU));
+    run(scheme, tau, nsteps, t0);
+    unpack_f32(F32(kU), host_stage_->ptr);
+    FCGLE_CUDA(cudaMemcpyAsync(uT, host_stage_->ptr, bytes, cudaMemcpyDeviceToHost, st_));
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  double norm(const void* u) override {
+    float* X = F32(kWork);
+    pack_f32((const float*)u, X);
+    sumsq<float>(s_, X, scratch_->ptr, st_, launches);
+    double h = 0.0;
+    FCGLE_CUDA(cudaMemcpyAsync(&h, scratch_->ptr, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+    double cell = 1.0;
+    for (int mu = 0; mu < s_.d; ++mu) cell *= h_[mu];
+    return std::sqrt(cell * h);
+  }
+
+ private:
+  enum { kU = 0, kUh, kFh, kD2, kD3, kEA, kUp, kWork, kNumF32 };
+  enum { kV = 0, kW, kT0, kT1, kNumSplit };
+
+  struct Mat {
+    __nv_bfloat16* hi = nullptr;
+    __nv_bfloat16* lo = nullptr;
+    int p = 0, m_pad = 0, k_pad = 0;
+    CUtensorMap tm_hi, tm_lo;
+  };
+
+  float* F32(int i) { return f32_[i]->ptr; }
+  SplitOut SP(int i) { return SplitOut{sp_[i]->ptr, sp_[i]->ptr + 2 * s_.P}; }
+
+  template <class Epi>
+  static void set_smem_attr() {
+    FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)b3::kSmemBytes));
+  }
+
+  void prepare_matrix(const double* M, int p, Mat& m) {
+    m.p = p;
+    m.m_pad = (p + b3::BM - 1) / b3::BM * b3::BM;
+    m.k_pad = (p + b3::BK - 1) / b3::BK * b3::BK;
+    std::vector<__nv_bfloat16> hi((size_t)m.m_pad * m.k_pad, __float2bfloat16(0.0f)), lo(hi);
+    for (int i = 0; i < p; ++i)
+      for (int k = 0; k < p; ++k) {
+        const double x = M[(size_t)i * p + k];
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+        hi[(size_t)i * m.k_pad + k] = h;
+        lo[(size_t)i * m.k_pad + k] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+      }
+    const size_t bytes = hi.size() * 2;
+    FCGLE_CUDA(cudaMalloc(&m.hi, bytes));
+    FCGLE_CUDA(cudaMalloc(&m.lo, bytes));
+    FCGLE_CUDA(cudaMemcpy(m.hi, hi.data(), bytes, cudaMemcpyHostToDevice));
+    FCGLE_CUDA(cudaMemcpy(m.lo, lo.data(), bytes, cudaMemcpyHostToDevice));
+    encode_bf16(&m.tm_hi, m.hi, m.k_pad, m.m_pad, b3::BM);
+    encode_bf16(&m.tm_lo, m.lo, m.k_pad, m.m_pad, b3::BM);
+  }
+
+  // one mode product of direction mu on split input (xh, xl) with epilogue epi
+  template <class Epi>
+  void launch_mp(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, const Epi& epi) {
+    const Mat& m = mat_[mu][fwd ? 0 : 1];
+    const long long R = P_ / s_.p[mu];
+    CUtensorMap txh, txl;
+    encode_bf16(&txh, xh, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    encode_bf16(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    b3::KParams kp;
+    kp.R = R;
+    kp.p = s_.p[mu];
+    kp.m_blocks = m.m_pad / b3::BM;
+    kp.k_chunks = m.k_pad / b3::BK;
+    kp.tiles = (R + b3::BR - 1) / b3::BR;
+    kp.err = err_->ptr;
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    b3::mp_b3_kernel<Epi><<<grid, b3::NTHREADS, b3::kSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, kp, epi);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  // Tucker operator on the split tensor `in` (consumed); the last mode product
+  // runs `epi`, which may write into `in` (d >= 2: `in` is only read by the
+  // first mode product; d == 1: `in` is first copied aside).
+  template <class Epi>
+  void tucker(SplitOut in, bool fwd, const Epi& epi) {
+    const int d = s_.d;
+    SplitOut src = in;
+    if (d == 1) {
+      SplitOut t = SP(kT1);
+      FCGLE_CUDA(cudaMemcpyAsync(t.hi, in.hi, 4 * s_.P * 2, cudaMemcpyDeviceToDevice, st_));
+      src = t;
+    }
+    for (int mu = 0; mu < d - 1; ++mu) {
+      SplitOut dst = SP(mu % 2 == 0 ? kT0 : kT1);
+      launch_mp(src.hi, src.lo, mu, fwd, b3::EpiStoreSplit{P_, dst});
+      src = dst;
+    }
+    launch_mp(src.hi, src.lo, d - 1, fwd, epi);
+  }
+
+  void pack_f32(const float* user, float* U) { pack<float>(s_, user, U, st_, launches); }
+  void unpack_f32(const float* U, float* user) { unpack<float>(s_, U, user, st_, launches); }
+
+  b3::GTime gtime(double t) const {
+    b3::GTime g;
+    for (int k = 0; k < gs_.nsrc; ++k) {
+      const double m = std::exp(sig_re_[k] * t);
+      g.e_re[k] = (float)(m * std::cos(sig_im_[k] * t));
+      g.e_im[k] = (float)(m * std::sin(sig_im_[k] * t));
+    }
+    return g;
+  }
+
+  // V = a u + b g(t, u) (+ optional V2)
+  void gsplit(const float* U, double t, float a, float b, SplitOut V, float a2 = 0.f, float b2 = 0.f,
+              SplitOut V2 = SplitOut{}) {
+    gsplit_kernel<<<grid_for(P_), 256, 0, st_>>>(P_, gs_, gtime(t), U, a, b, V, a2, b2, V2);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  b3::Flow flow(double t) const {
+    const double z = 2.0 * prm_.gamma * t;
+    const double p1 = std::fabs(z) < 1e-8 ? 1.0 + z / 2.0 : std::expm1(z) / z;
+    b3::Flow f;
+    f.gamma_t = (float)(t * prm_.gamma);
+    f.c2 = (float)(2.0 * t * p1 * prm_.kappa);
+    f.zk = (float)(prm_.zeta / (2.0 * prm_.kappa));
+    return f;
+  }
+
+  const float* Ften(int func, int ell, double theta) {
+    if (func == FCGLE_F_PHI && ell == 0) func = FCGLE_F_EXP;
+    if (func != FCGLE_F_PHI) ell = 0;
+    auto key = std::make_tuple(func, ell, bits_of(theta));
+    auto it = fcache_.find(key);
+    if (it != fcache_.end()) return it->second->ptr;
+    auto* b = new DevMem<float>(2 * s_.P);
+    fcache_[key].reset(b);
+    fill_F<float>(s_, lv_, func, ell, theta, b->ptr, st_, launches);
+    return b->ptr;
+  }
+
+  void prepare(int scheme, double tau) {
+    switch (scheme) {
+      case FCGLE_LIE: Ften(FCGLE_F_INV, 0, tau); break;
+      case FCGLE_LBDF2: Ften(FCGLE_F_INV, 0, tau); Ften(FCGLE_F_INV, 0, 2.0 * tau / 3.0); break;
+      case FCGLE_LAWSON_EULER:
+      case FCGLE_LAWSON_RK2:
+      case FCGLE_STRANG: Ften(FCGLE_F_EXP, 0, tau); break;
+      case FCGLE_ETD2RK: Ften(FCGLE_F_PHI, 1, tau); Ften(FCGLE_F_PHI, 2, tau); break;
+      case FCGLE_KROGSTAD:
+        Ften(FCGLE_F_PHI, 1, tau / 2); Ften(FCGLE_F_PHI, 2, tau / 2);
+        Ften(FCGLE_F_PHI, 1, tau); Ften(FCGLE_F_PHI, 2, tau); Ften(FCGLE_F_PHI, 3, tau);
+        break;
+      default: throw InvalidArg("unknown scheme");
+    }
+  }
+
+  // prologue (entry state of the loop), then nsteps fused steps on F32(kU)
+  void run(int scheme, double tau, int nsteps, double t0) {
+    prepare(scheme, tau);
+    if (nsteps == 0) return;
+    float* U = F32(kU);
+    SplitOut V = SP(kV), W = SP(kW);
+    const float ft = (float)tau;
+    switch (scheme) {
+      case FCGLE_LIE:
+      case FCGLE_LAWSON_EULER: {
+        const float* F = Ften(scheme == FCGLE_LIE ? FCGLE_F_INV : FCGLE_F_EXP, 0, tau);
+        gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
+        for (int n = 0; n < nsteps; ++n) {
+          tucker(V, true, b3::EpiScaleSplit{P_, F, V});
+          tucker(V, false, b3::EpiUpdateG{P_, U, 0, gs_, gtime(t0 + (n + 1) * tau), 1.f, ft, V});
+        }
+        break;
+      }
+      case FCGLE_STRANG: {
+        const float* E = Ften(FCGLE_F_EXP, 0, tau);
+        const b3::Flow f = flow(tau / 2);
+        flow_split_kernel<<<grid_for(P_), 256, 0, st_>>>(P_, f, U, V);
+        FCGLE_LAUNCHED(launches);
+        for (int n = 0; n < nsteps; ++n) {
+          tucker(V, true, b3::EpiScaleSplit{P_, E, V});
+          tucker(V, false, b3::EpiStrang{P_, U, f, V});
+        }
+        break;
+      }
+      case FCGLE_LAWSON_RK2: {
+        const float* E = Ften(FCGLE_F_EXP, 0, tau);
+        float* EA = F32(kEA);
+        gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
+        for (int n = 0; n < nsteps; ++n) {
+          tucker(V, true, b3::EpiScaleSplit{P_, E, V});
+          tucker(V, false, b3::EpiStoreF32{P_, EA});
+          tucker(W, true, b3::EpiScaleSplit{P_, E, W});
+          tucker(W, false, b3::EpiLawsonRK2{P_, U, EA, gs_, gtime(t0 + (n + 1) * tau), ft, V, W});
+        }
+        break;
+      }
+      case FCGLE_LBDF2: {
+        const float* R1 = Ften(FCGLE_F_INV, 0, tau);
+        const float* R23 = Ften(FCGLE_F_INV, 0, 2.0 * tau / 3.0);
+        float* Up = F32(kUp);
+        // first step: linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps
+        // u_0 as u_{n-1} and forms the first LBDF2 right-hand side
+        gsplit(U, t0, 1.f, ft, V);
+        tucker(V, true, b3::EpiScaleSplit{P_, R1, V});
+        tucker(V, false, b3::EpiLBDF2{P_, U, Up, gs_, gtime(t0 + 2 * tau), ft, V});
+        for (int n = 1; n < nsteps; ++n) {
+          tucker(V, true, b3::EpiScaleSplit{P_, R23, V});
+          tucker(V, false, b3::EpiLBDF2{P_, U, Up, gs_, gtime(t0 + (n + 2) * tau), ft, V});
+        }
+        break;
+      }
+      case FCGLE_ETD2RK: {
+        const float* P1 = Ften(FCGLE_F_PHI, 1, tau);
+        const float* P2 = Ften(FCGLE_F_PHI, 2, tau);
+        float *Uh = F32(kUh), *Fh = F32(kFh);
+        gsplit(U, t0, 1.f, 0.f, V);                              // U^_0 = fwd(u_0)
+        tucker(V, true, b3::EpiStoreF32{P_, Uh});
+        gsplit(U, t0, 0.f, 1.f, V);                              // G_0
+        for (int n = 0; n < nsteps; ++n) {
+          const double t = t0 + n * tau;
+          // S1 = tau P1 o (Lam o U^ + G^);  a^ = U^ + S1
+          tucker(V, true, b3::EpiFhat{P_, lf_, Uh, Fh, P1, ft, 1, V});
+          // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
+          tucker(V, false, b3::EpiStageD{P_, U, U, gs_, gtime(t + tau), gtime(t), V});
+          // S2 = tau P2 o D^;  U^ += S2
+          tucker(V, true, b3::EpiStage2{P_, nullptr, nullptr, 0.f, P2, ft, nullptr, Uh, V});
+          // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
+          tucker(V, false, b3::EpiUpdateG{P_, U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
+        }
+        break;
+      }
+      case FCGLE_KROGSTAD: {
+        const float* P1h = Ften(FCGLE_F_PHI, 1, tau / 2);
+        const float* P2h = Ften(FCGLE_F_PHI, 2, tau / 2);
+        const float* P1 = Ften(FCGLE_F_PHI, 1, tau);
+        const float* P2 = Ften(FCGLE_F_PHI, 2, tau);
+        const float* P3 = Ften(FCGLE_F_PHI, 3, tau);
+        float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *D3 = F32(kD3);
+        gsplit(U, t0, 1.f, 0.f, V);
+        tucker(V, true, b3::EpiStoreF32{P_, Uh});
+        gsplit(U, t0, 0.f, 1.f, V);
+        for (int n = 0; n < nsteps; ++n) {
+          const double t = t0 + n * tau;
+          const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
+          // F^ = Lam o U^ + G^;  S = tau/2 P1(tau/2) F^
+          tucker(V, true, b3::EpiFhat{P_, lf_, Uh, Fh, P1h, 0.5f * ft, 0, V});
+          // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
+          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, th, tn, V});
+          // D^_2;  S = tau (1/2 P1(tau/2) F^ + P2(tau/2) D^_2)
+          tucker(V, true, b3::EpiStage2{P_, Fh, P1h, 0.5f * ft, P2h, ft, D2, nullptr, V});
+          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, th, tn, V});
+          // D^_3;  S = tau (P1(tau) F^ + 2 P2(tau) D^_3)
+          tucker(V, true, b3::EpiStage2{P_, Fh, P1, ft, P2, 2.f * ft, D3, nullptr, V});
+          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, t1, tn, V});
+          // D^_4;  final combination;  U^ += S
+          tucker(V, true, b3::EpiKrogFinal{P_, Fh, D2, D3, P1, P2, P3, Uh, ft, V});
+          // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
+          tucker(V, false, b3::EpiUpdateG{P_, U, 1, gs_, t1, 0.f, 1.f, V});
+        }
+        break;
+      }
+      default: throw InvalidArg("unknown scheme");
+    }
+  }
+
+  fcgle_params prm_;
+  cudaStream_t st_;
+  Shape s_;
+  long long P_ = 0;
+  double h_[kMaxDim] = {1, 1, 1};
+  Mat mat_[kMaxDim][2];
+  std::unique_ptr<DevMem<double>> lam_[kMaxDim];
+  std::unique_ptr<DevMem<float>> lamf_[kMaxDim];
+  LamVecs lv_{};
+  b3::LamF lf_{};
+  b3::GStatic gs_{};
+  double sig_re_[kMaxSrc] = {0, 0, 0, 0}, sig_im_[kMaxSrc] = {0, 0, 0, 0};
+  std::unique_ptr<DevMem<float>> f32_[kNumF32];
+  std::unique_ptr<DevMem<__nv_bfloat16>> sp_[kNumSplit];
+  std::unique_ptr<DevMem<float>> src_[kMaxSrc];
+  std::unique_ptr<DevMem<float>> host_stage_;
+  std::unique_ptr<DevMem<double>> scratch_;
+  std::unique_ptr<DevMem<int>> err_;
+  std::map<std::tuple<int, int, uint64_t>, std::unique_ptr<DevMem<float>>> fcache_;
+};
+
+std::unique_ptr<EngineBase> make_engine_b3(const fcgle_params& prm, cudaStream_t st) {
+  return std::unique_ptr<EngineBase>(new EngineB3(prm, st));
+}
+
+}  // namespace fcgle

@@ -200,8 +200,9 @@ def fcgle_internal_elems(h):
 
 
 def fcgle_mode_product(h, direction, forward, X, Y):
-    """X, Y: flat device tensors of 2 P reals (float64 / float32) in the internal layout."""
-    _check(_lib.fcgle_mode_product(h, int(direction), int(bool(forward)), _ptr(X), _ptr(Y)))
+    """X, Y: flat device tensors in the internal layout: 2 P reals (float64 / float32), or with
+    forward bit 1 set (BF16X3 handles) 4 P bf16 (hi planes, then lo planes)."""
+    _check(_lib.fcgle_mode_product(h, int(direction), int(forward), _ptr(X), _ptr(Y)))
 
 
 def fcgle_destroy(h):

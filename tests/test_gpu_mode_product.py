@@ -60,10 +60,11 @@ def test_unit_vectors_give_eigenvectors(fc, prec, tol):
 
 
 def test_bf16x3_matches_fp64_kernel(fc):
-    ns = [30, 130, 9]                     # p = (32, 132, 12): 2 i-blocks, 3 k-chunks in direction 2
+    ns = [30, 134, 14]                    # p = (32, 136, 16) in both layouts: 2 i-blocks, 3 k-chunks in direction 2
     s64, _, _ = _solver(fc, ns, "fp64")
     s32, _, _ = _solver(fc, ns, "bf16x3")
     P = fc.fcgle_internal_elems(s64.h)
+    assert fc.fcgle_internal_elems(s32.h) == P
     gen = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn(2 * P, device="cuda", dtype=torch.float64, generator=gen)
     for mu in range(3):
@@ -78,3 +79,28 @@ def test_bf16x3_matches_fp64_kernel(fc):
             assert err <= 3e-5, (mu, fwd, err)
     s64.close()
     s32.close()
+
+
+def _split(x):
+    hi = x.to(torch.bfloat16)
+    lo = (x - hi.float()).to(torch.bfloat16)
+    return torch.cat([hi, lo])
+
+
+def test_split_io_equals_fp32_io(fc):
+    # flags bit 1: the kernel's own input/output format (hi plane pair, then lo)
+    ns = [40, 24, 16]
+    s, _, _ = _solver(fc, ns, "bf16x3")
+    P = fc.fcgle_internal_elems(s.h)
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    X = torch.randn(2 * P, device="cuda", dtype=torch.float32, generator=gen)
+    for mu in range(3):
+        Y32 = torch.empty_like(X)
+        fc.fcgle_mode_product(s.h, mu, 1, X, Y32)
+        Ys = torch.empty(4 * P, device="cuda", dtype=torch.bfloat16)
+        fc.fcgle_mode_product(s.h, mu, 1 | 2, _split(X), Ys)
+        s.sync()
+        y = Ys[: 2 * P].float() + Ys[2 * P:].float()
+        err = float(torch.linalg.vector_norm(y - Y32) / torch.linalg.vector_norm(Y32))
+        assert err <= 1e-5, (mu, err)
+    s.close()
