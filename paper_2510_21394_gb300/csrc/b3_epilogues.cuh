@@ -8,7 +8,11 @@
 //   * Hadamard products with the spectral tensors F = f(theta lam) (Eq. fKu_diag),
 //   * the stage combinations of Eq. krogstad-m and the other schemes,
 // writing FP32 planar tensors and/or split (hi, lo) bf16 tensors that feed
-// the next mode product.  Each functor is a plain struct passed by value.
+// the next mode product.  Each functor is a plain struct passed by value with
+//   kTmaStore  true: no functor call, the kernel stores the product split
+//              through TMA bulk tensor stores (needs R % 8 == 0);
+//   kIn, kBatch, load(q, i, r, in), store(q, i, r, re, im, in): the kernel
+//              loads the operands of kBatch elements first, then stores.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -81,35 +85,63 @@ __device__ __forceinline__ void cmul(float ar, float ai, float br, float bi, flo
 }
 
 // ---------------------------------------------------------------- functors
+#define FCGLE_EPI(IN, BATCH)              \
+  static constexpr bool kTmaStore = false; \
+  static constexpr int kIn = IN;           \
+  static constexpr int kBatch = BATCH;
+
+// product -> split, through TMA stores
 struct EpiStoreSplit {
-  long long P;
-  SplitOut Y;
-  __device__ void operator()(long long q, int, long long, float re, float im) const { put_csplit(Y, P, q, re, im); }
+  static constexpr bool kTmaStore = true;
+  static constexpr int kIn = 0;
+  static constexpr int kBatch = 1;
+  __device__ void load(long long, int, long long, float*) const {}
+  __device__ void store(long long, int, long long, float, float, const float*) const {}
 };
 
+// product -> split, element stores (any R)
+struct EpiStoreSplitGen {
+  FCGLE_EPI(0, 8)
+  long long P;
+  SplitOut Y;
+  __device__ void load(long long, int, long long, float*) const {}
+  __device__ void store(long long q, int, long long, float re, float im, const float*) const {
+    put_csplit(Y, P, q, re, im);
+  }
+};
+
+// product -> FP32
 struct EpiStoreF32 {
+  FCGLE_EPI(0, 8)
   long long P;
   float* Y;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long, int, long long, float*) const {}
+  __device__ void store(long long q, int, long long, float re, float im, const float*) const {
     Y[q] = re;
     Y[P + q] = im;
   }
 };
 
-// Y = F o acc  (split)
+// Y = F o product  (split)
 struct EpiScaleSplit {
+  FCGLE_EPI(2, 8)
   long long P;
   const float* F;
   SplitOut Y;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = __ldg(F + q);
+    in[1] = __ldg(F + P + q);
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
     float yr, yi;
-    cmul(F[q], F[P + q], re, im, yr, yi);
+    cmul(in[0], in[1], re, im, yr, yi);
     put_csplit(Y, P, q, yr, yi);
   }
 };
 
-// u = (add ? U : 0) + acc -> U (FP32);  V = a u + b g(t', u) -> split
+// u = (add ? U : 0) + product -> U (FP32);  V = a u + b g(t', u) -> split
 struct EpiUpdateG {
+  FCGLE_EPI(2, 8)
   long long P;
   float* U;
   int add;
@@ -117,11 +149,17 @@ struct EpiUpdateG {
   GTime t;
   float a, b;
   SplitOut V;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long q, int, long long, float* in) const {
+    if (add) {
+      in[0] = U[q];
+      in[1] = U[P + q];
+    }
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
     float ur = re, ui = im;
     if (add) {
-      ur += U[q];
-      ui += U[P + q];
+      ur += in[0];
+      ui += in[1];
     }
     U[q] = ur;
     U[P + q] = ui;
@@ -131,16 +169,21 @@ struct EpiUpdateG {
   }
 };
 
-// u_s = U + acc;  D = g(t_s, u_s) - g(t_n, U) -> split;  optionally U_out = u_s
+// u_s = U + product;  D = g(t_s, u_s) - g(t_n, U) -> split;  optionally U_out = u_s
 struct EpiStageD {
+  FCGLE_EPI(2, 8)
   long long P;
   const float* U;
   float* Uout;
   GStatic g;
   GTime ts, tn;
   SplitOut D;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
-    const float ur = U[q], ui = U[P + q];
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = U[q];
+    in[1] = U[P + q];
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
+    const float ur = in[0], ui = in[1];
     const float sr = ur + re, si = ui + im;
     float g1r, g1i, g0r, g0i;
     g_eval(g, ts, P, q, sr, si, g1r, g1i);
@@ -153,8 +196,9 @@ struct EpiStageD {
   }
 };
 
-// G^ = acc;  F^ = Lam o U^ + G^ -> Fh;  S = c P1 o F^ -> split;  optionally U^ += S
+// G^ = product;  F^ = Lam o U^ + G^ -> Fh;  S = c P1 o F^ -> split;  optionally U^ += S
 struct EpiFhat {
+  FCGLE_EPI(4, 8)
   long long P;
   LamF L;
   float* Uh;
@@ -163,30 +207,36 @@ struct EpiFhat {
   float c;
   int update_uh;
   SplitOut S;
-  __device__ void operator()(long long q, int i, long long r, float re, float im) const {
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = Uh[q];
+    in[1] = Uh[P + q];
+    in[2] = __ldg(P1 + q);
+    in[3] = __ldg(P1 + P + q);
+  }
+  __device__ void store(long long q, int i, long long r, float re, float im, const float* in) const {
     float lr, li;
     lam_eval(L, i, r, lr, li);
-    const float uhr = Uh[q], uhi = Uh[P + q];
     float fr, fi;
-    cmul(lr, li, uhr, uhi, fr, fi);
+    cmul(lr, li, in[0], in[1], fr, fi);
     fr += re;
     fi += im;
     Fh[q] = fr;
     Fh[P + q] = fi;
     float sr, si;
-    cmul(P1[q], P1[P + q], fr, fi, sr, si);
+    cmul(in[2], in[3], fr, fi, sr, si);
     sr *= c;
     si *= c;
     put_csplit(S, P, q, sr, si);
     if (update_uh) {
-      Uh[q] = uhr + sr;
-      Uh[P + q] = uhi + si;
+      Uh[q] = in[0] + sr;
+      Uh[P + q] = in[1] + si;
     }
   }
 };
 
-// D^ = acc -> Dsave (optional);  S = a Pa o F^ + b Pb o D^ -> split;  optionally U^ += S
+// D^ = product -> Dsave (optional);  S = a Pa o F^ + b Pb o D^ -> split;  optionally U^ += S
 struct EpiStage2 {
+  FCGLE_EPI(8, 4)
   long long P;
   const float* Fh;   // may be null when a == 0
   const float* Pa;
@@ -196,25 +246,39 @@ struct EpiStage2 {
   float* Dsave;
   float* Uh;         // null: no update
   SplitOut S;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = __ldg(Pb + q);
+    in[1] = __ldg(Pb + P + q);
+    if (a != 0.f) {
+      in[2] = __ldg(Pa + q);
+      in[3] = __ldg(Pa + P + q);
+      in[4] = __ldg(Fh + q);
+      in[5] = __ldg(Fh + P + q);
+    }
+    if (Uh) {
+      in[6] = Uh[q];
+      in[7] = Uh[P + q];
+    }
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
     if (Dsave) {
       Dsave[q] = re;
       Dsave[P + q] = im;
     }
     float sr, si;
-    cmul(Pb[q], Pb[P + q], re, im, sr, si);
+    cmul(in[0], in[1], re, im, sr, si);
     sr *= b;
     si *= b;
     if (a != 0.f) {
       float tr, ti;
-      cmul(Pa[q], Pa[P + q], Fh[q], Fh[P + q], tr, ti);
+      cmul(in[2], in[3], in[4], in[5], tr, ti);
       sr += a * tr;
       si += a * ti;
     }
     put_csplit(S, P, q, sr, si);
     if (Uh) {
-      Uh[q] += sr;
-      Uh[P + q] += si;
+      Uh[q] = in[6] + sr;
+      Uh[P + q] = in[7] + si;
     }
   }
 };
@@ -222,32 +286,49 @@ struct EpiStage2 {
 // Krogstad's last combination (Eq. krogstad-m):
 // S = tau (P1 F^ + P2 (2 D2 + 2 D3 - D4) + P3 (-4 D2 - 4 D3 + 4 D4)) -> split; U^ += S
 struct EpiKrogFinal {
+  FCGLE_EPI(14, 4)
   long long P;
   const float *Fh, *D2, *D3, *P1, *P2, *P3;
   float* Uh;
   float tau;
   SplitOut S;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
-    const float d2r = D2[q], d2i = D2[P + q], d3r = D3[q], d3i = D3[P + q];
-    const float br = 2.f * d2r + 2.f * d3r - re, bi = 2.f * d2i + 2.f * d3i - im;
-    const float cr = 4.f * (re - d2r - d3r), ci = 4.f * (im - d2i - d3i);
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = __ldg(Fh + q);
+    in[1] = __ldg(Fh + P + q);
+    in[2] = __ldg(D2 + q);
+    in[3] = __ldg(D2 + P + q);
+    in[4] = __ldg(D3 + q);
+    in[5] = __ldg(D3 + P + q);
+    in[6] = __ldg(P1 + q);
+    in[7] = __ldg(P1 + P + q);
+    in[8] = __ldg(P2 + q);
+    in[9] = __ldg(P2 + P + q);
+    in[10] = __ldg(P3 + q);
+    in[11] = __ldg(P3 + P + q);
+    in[12] = Uh[q];
+    in[13] = Uh[P + q];
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
+    const float br = 2.f * in[2] + 2.f * in[4] - re, bi = 2.f * in[3] + 2.f * in[5] - im;
+    const float cr = 4.f * (re - in[2] - in[4]), ci = 4.f * (im - in[3] - in[5]);
     float sr, si, tr, ti;
-    cmul(P1[q], P1[P + q], Fh[q], Fh[P + q], sr, si);
-    cmul(P2[q], P2[P + q], br, bi, tr, ti);
+    cmul(in[6], in[7], in[0], in[1], sr, si);
+    cmul(in[8], in[9], br, bi, tr, ti);
     sr += tr;
     si += ti;
-    cmul(P3[q], P3[P + q], cr, ci, tr, ti);
+    cmul(in[10], in[11], cr, ci, tr, ti);
     sr = tau * (sr + tr);
     si = tau * (si + ti);
     put_csplit(S, P, q, sr, si);
-    Uh[q] += sr;
-    Uh[P + q] += si;
+    Uh[q] = in[12] + sr;
+    Uh[P + q] = in[13] + si;
   }
 };
 
-// LBDF2 (Eq. lbdf2-v): u_{n+1} = acc -> U, u_n -> Uprev;
+// LBDF2 (Eq. lbdf2-v): u_{n+1} = product -> U, u_n -> Uprev;
 // next right-hand side 4/3 u_{n+1} - 1/3 u_n + 2 tau/3 g(t_{n+2}, 2 u_{n+1} - u_n) -> split
 struct EpiLBDF2 {
+  FCGLE_EPI(2, 8)
   long long P;
   float* U;
   float* Uprev;
@@ -255,8 +336,12 @@ struct EpiLBDF2 {
   GTime t;
   float tau;
   SplitOut V;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
-    const float or_ = U[q], oi = U[P + q];
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = U[q];
+    in[1] = U[P + q];
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
+    const float or_ = in[0], oi = in[1];
     Uprev[q] = or_;
     Uprev[P + q] = oi;
     U[q] = re;
@@ -268,9 +353,10 @@ struct EpiLBDF2 {
   }
 };
 
-// Lawson-RK2 (Heun): u_{n+1} = acc + tau/2 g(t_{n+1}, EA) -> U;
+// Lawson-RK2 (Heun): u_{n+1} = product + tau/2 g(t_{n+1}, EA) -> U;
 // next k1 = g(t_{n+1}, u_{n+1}); A = u + tau k1, B = u + tau/2 k1 -> split
 struct EpiLawsonRK2 {
+  FCGLE_EPI(2, 8)
   long long P;
   float* U;
   const float* EA;
@@ -278,9 +364,13 @@ struct EpiLawsonRK2 {
   GTime t;   // t_{n+1}
   float tau;
   SplitOut A, Bv;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long q, int, long long, float* in) const {
+    in[0] = __ldg(EA + q);
+    in[1] = __ldg(EA + P + q);
+  }
+  __device__ void store(long long q, int, long long, float re, float im, const float* in) const {
     float gr, gi;
-    g_eval(g, t, P, q, EA[q], EA[P + q], gr, gi);
+    g_eval(g, t, P, q, in[0], in[1], gr, gi);
     const float ur = re + 0.5f * tau * gr, ui = im + 0.5f * tau * gi;
     U[q] = ur;
     U[P + q] = ui;
@@ -306,13 +396,15 @@ __device__ __forceinline__ void flow_eval(const Flow& f, float wr, float wi, flo
   yi = m * (c * wi + s * wr);
 }
 
-// Strang (Eq. Strang): u_{n+1} = Phi(acc) -> U;  next V = Phi(u_{n+1}) -> split
+// Strang (Eq. Strang): u_{n+1} = Phi(product) -> U;  next V = Phi(u_{n+1}) -> split
 struct EpiStrang {
+  FCGLE_EPI(0, 8)
   long long P;
   float* U;
   Flow f;
   SplitOut V;
-  __device__ void operator()(long long q, int, long long, float re, float im) const {
+  __device__ void load(long long, int, long long, float*) const {}
+  __device__ void store(long long q, int, long long, float re, float im, const float*) const {
     float ur, ui, vr, vi;
     flow_eval(f, re, im, ur, ui);
     U[q] = ur;
@@ -321,6 +413,8 @@ struct EpiStrang {
     put_csplit(V, P, q, vr, vi);
   }
 };
+
+#undef FCGLE_EPI
 
 }  // namespace b3
 }  // namespace fcgle

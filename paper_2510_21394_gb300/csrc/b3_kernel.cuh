@@ -20,9 +20,11 @@
 //   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x 64 x 64)
 //               bf16 chunks, SWIZZLE_128B, straight into the MMA layout.
 //   warp 1      TMEM allocator and single-thread MMA issuer (3 MMAs per k-step).
-//   warps 2-9   epilogue: TMEM -> registers -> smem transpose -> functor on
-//               coalesced (i, r) runs.  Warp w reads TMEM lane quarter w % 4 and
-//               column groups (w - 2) / 4 and (w - 2) / 4 + 2.
+//   warps 2-9   epilogue: TMEM -> registers, then either split + TMA bulk
+//               tensor stores of 32 x 16 boxes (plain mode products), or an
+//               smem transpose and a functor on coalesced (i, r) runs.  Warp w
+//               reads TMEM lane quarter w % 4 and column groups (w - 2) / 4 and
+//               (w - 2) / 4 + 2.
 // Pipelines: 3 smem stages (64 KB each), 2 TMEM accumulators (2 x 128 columns).
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error code in *err, drains its own TMA and MMA work, frees its
@@ -146,10 +148,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ kernel
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t split_pair(float a, float b, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Epilogue functor interface (b3_epilogues.cuh): either kTmaStore (the
+// product is stored split through tm_yhi / tm_ylo, no functor call), or a
+// batched two-phase functor: load(q, i, r, in) for kBatch elements, then
+// store(q, i, r, re, im, in) for each, so that the operand loads of a batch
+// are in flight together.
 template <class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
+                 const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                  const KParams kp, const Epi epi) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -278,20 +304,67 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tmem_ld16(tl, vr);
         tmem_ld16(tl + BR, vi);
         tmem_wait_ld();
+        if constexpr (Epi::kTmaStore) {
+          // four 32 x 16 bf16 boxes (re hi, re lo, im hi, im lo); row = this lane's i
+          uint32_t* box = reinterpret_cast<uint32_t*>(stg);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          stg[lane * 33 + j] = __uint_as_float(vr[j]);
-          stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
+          for (int j = 0; j < 16; j += 8) {
+            uint4 rh, rl, ih, il;
+            rh.x = split_pair(__uint_as_float(vr[j + 0]), __uint_as_float(vr[j + 1]), rl.x);
+            rh.y = split_pair(__uint_as_float(vr[j + 2]), __uint_as_float(vr[j + 3]), rl.y);
+            rh.z = split_pair(__uint_as_float(vr[j + 4]), __uint_as_float(vr[j + 5]), rl.z);
+            rh.w = split_pair(__uint_as_float(vr[j + 6]), __uint_as_float(vr[j + 7]), rl.w);
+            ih.x = split_pair(__uint_as_float(vi[j + 0]), __uint_as_float(vi[j + 1]), il.x);
+            ih.y = split_pair(__uint_as_float(vi[j + 2]), __uint_as_float(vi[j + 3]), il.y);
+            ih.z = split_pair(__uint_as_float(vi[j + 4]), __uint_as_float(vi[j + 5]), il.z);
+            ih.w = split_pair(__uint_as_float(vi[j + 6]), __uint_as_float(vi[j + 7]), il.w);
+            const int w = lane * 8 + j / 2;   // 32-bit word of this row's 16 bf16
+            *reinterpret_cast<uint4*>(box + 0 * 256 + w) = rh;
+            *reinterpret_cast<uint4*>(box + 1 * 256 + w) = rl;
+            *reinterpret_cast<uint4*>(box + 2 * 256 + w) = ih;
+            *reinterpret_cast<uint4*>(box + 3 * 256 + w) = il;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            const int x = (int)(tile * BR + cc * 16);
+            const uint32_t sb = smem_u32(box);
+            tma_store_3d(&tm_yhi, sb + 0 * 1024, x, i_base, 0);
+            tma_store_3d(&tm_ylo, sb + 1 * 1024, x, i_base, 0);
+            tma_store_3d(&tm_yhi, sb + 2 * 1024, x, i_base, 1);
+            tma_store_3d(&tm_ylo, sb + 3 * 1024, x, i_base, 1);
+            bulk_commit();
+            bulk_wait_read0();   // staging reusable once the stores have read it
+          }
+          __syncwarp();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            stg[lane * 33 + j] = __uint_as_float(vr[j]);
+            stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
+          }
+          __syncwarp();
+          const long long r = tile * BR + cc * 16 + rr;
+          constexpr int B = Epi::kBatch;
+          constexpr int NI = Epi::kIn > 0 ? Epi::kIn : 1;
+#pragma unroll 1
+          for (int it0 = 0; it0 < 16; it0 += B) {
+            float in[B][NI];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+              const int i = i_base + it0 + b + hrow;
+              if (i < kp.p && r < kp.R) epi.load((long long)i * kp.R + r, i, r, in[b]);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+              const int ii = it0 + b + hrow;
+              const int i = i_base + ii;
+              if (i < kp.p && r < kp.R)
+                epi.store((long long)i * kp.R + r, i, r, stg[ii * 33 + rr], stg[ii * 33 + 16 + rr], in[b]);
+            }
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        const long long r = tile * BR + cc * 16 + rr;
-#pragma unroll 2
-        for (int it = 0; it < 16; ++it) {
-          const int ii = it + hrow;
-          const int i = i_base + ii;
-          if (i < kp.p && r < kp.R) epi((long long)i * kp.R + r, i, r, stg[ii * 33 + rr], stg[ii * 33 + 16 + rr]);
-        }
-        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -299,6 +372,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
 
+  if constexpr (Epi::kTmaStore) {
+    if (warp >= 2 && lane == 0) bulk_wait0();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

@@ -85,6 +85,19 @@ void encode_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ro
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
+// 3D bf16 tensor map over a split output plane pair [2][p][R], box (16, 32, 1),
+// no swizzle: the TMA-store epilogue writes 32 x 16 element boxes.
+void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p) {
+  cuuint64_t dims[3] = {R, p, 2};
+  cuuint64_t strides[2] = {R * 2, R * p * 2};
+  cuuint32_t box[3] = {16, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
+}
+
 // ------------------------------------------------------ standalone kernels
 // V = a u + b g(t, u) (split); optionally V2 = a2 u + b2 g(t, u) (split)
 __global__ void gsplit_kernel(long long P, b3::GStatic g, b3::GTime t, const float* __restrict__ U, float a, float b,
@@ -187,6 +200,7 @@ class EngineB3 : public EngineBase {
     static bool attrs = false;
     if (!attrs) {
       set_smem_attr<b3::EpiStoreSplit>();
+      set_smem_attr<b3::EpiStoreSplitGen>();
       set_smem_attr<b3::EpiStoreF32>();
       set_smem_attr<b3::EpiScaleSplit>();
       set_smem_attr<b3::EpiUpdateG>();
@@ -242,7 +256,7 @@ class EngineB3 : public EngineBase {
       const __nv_bfloat16* xh = (const __nv_bfloat16*)X;
       __nv_bfloat16* yh = (__nv_bfloat16*)Y;
       SplitOut out{yh, yh + 2 * s_.P};
-      launch_mp(xh, xh + 2 * s_.P, mu, fwd, b3::EpiStoreSplit{P_, out});
+      store_split(xh, xh + 2 * s_.P, mu, fwd, out);
     } else {
       SplitOut t = SP(kT0);
       to_split_kernel<<<grid_for(2 * P_), 256, 0, st_>>>(2 * P_, (const float*)X, t);
@@ -341,9 +355,19 @@ class EngineB3 : public EngineBase {
     encode_bf16(&m.tm_lo, m.lo, m.k_pad, m.m_pad, b3::BM);
   }
 
+  // mode product with a split output: TMA stores when the output rows allow
+  void store_split(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, SplitOut out) {
+    const long long R = P_ / s_.p[mu];
+    if (R % 8 == 0)
+      launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplit{}, &out);
+    else
+      launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplitGen{P_, out});
+  }
+
   // one mode product of direction mu on split input (xh, xl) with epilogue epi
   template <class Epi>
-  void launch_mp(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, const Epi& epi) {
+  void launch_mp(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, const Epi& epi,
+                 const SplitOut* tma_out = nullptr) {
     const Mat& m = mat_[mu][fwd ? 0 : 1];
     const long long R = P_ / s_.p[mu];
     CUtensorMap txh, txl;
@@ -358,7 +382,13 @@ class EngineB3 : public EngineBase {
     kp.err = err_->ptr;
     const long long units = kp.tiles * kp.m_blocks;
     const int grid = (int)std::min<long long>(units, num_sms());
-    b3::mp_b3_kernel<Epi><<<grid, b3::NTHREADS, b3::kSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, kp, epi);
+    CUtensorMap tyh = txh, tyl = txl;   // unused unless the epilogue stores through TMA
+    if (Epi::kTmaStore) {
+      if (!tma_out) throw std::runtime_error("TMA-store epilogue without an output");
+      encode_bf16_out(&tyh, tma_out->hi, (uint64_t)R, (uint64_t)s_.p[mu]);
+      encode_bf16_out(&tyl, tma_out->lo, (uint64_t)R, (uint64_t)s_.p[mu]);
+    }
+    b3::mp_b3_kernel<Epi><<<grid, b3::NTHREADS, b3::kSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, epi);
     FCGLE_LAUNCHED(launches);
   }
 
@@ -376,7 +406,7 @@ class EngineB3 : public EngineBase {
     }
     for (int mu = 0; mu < d - 1; ++mu) {
       SplitOut dst = SP(mu % 2 == 0 ? kT0 : kT1);
-      launch_mp(src.hi, src.lo, mu, fwd, b3::EpiStoreSplit{P_, dst});
+      store_split(src.hi, src.lo, mu, fwd, dst);
       src = dst;
     }
     launch_mp(src.hi, src.lo, d - 1, fwd, epi);
