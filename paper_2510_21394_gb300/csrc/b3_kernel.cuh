@@ -344,23 +344,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
           }
           __syncwarp();
-          const long long r = tile * BR + cc * 16 + rr;
           constexpr int B = Epi::kBatch;
           constexpr int NI = Epi::kIn > 0 ? Epi::kIn : 1;
+          const uint32_t R32 = (uint32_t)kp.R;
+          if ((R32 & 3u) == 0) {
+            // 4 consecutive r per lane: lane = 4 a + k covers rows a, a + 8, .. and r = 16 cc + 4 k + 0..3
+            const int k4 = lane & 3, a8 = lane >> 2;
+            const uint32_t r = (uint32_t)(tile * BR + cc * 16 + 4 * k4);
 #pragma unroll 1
-          for (int it0 = 0; it0 < 16; it0 += B) {
-            float in[B][NI];
+            for (int it0 = 0; it0 < 4; it0 += B) {
+              float in[B][NI][4];
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-              const int i = i_base + it0 + b + hrow;
-              if (i < kp.p && r < kp.R) epi.load((long long)i * kp.R + r, i, r, in[b]);
+              for (int b = 0; b < B; ++b) {
+                const int i = i_base + a8 + 8 * (it0 + b);
+                if (i < kp.p && r < R32) epi.template load<4>((uint32_t)i * R32 + r, i, r, in[b]);
+              }
+#pragma unroll
+              for (int b = 0; b < B; ++b) {
+                const int ii = a8 + 8 * (it0 + b);
+                const int i = i_base + ii;
+                if (i < kp.p && r < R32) {
+                  float re[4], im[4];
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) {
+                    re[v] = stg[ii * 33 + 4 * k4 + v];
+                    im[v] = stg[ii * 33 + 16 + 4 * k4 + v];
+                  }
+                  epi.template store<4>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
+                }
+              }
             }
+          } else {
+            const uint32_t r = (uint32_t)(tile * BR + cc * 16 + rr);
+#pragma unroll 1
+            for (int it0 = 0; it0 < 16; it0 += B) {
+              float in[B][NI][1];
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-              const int ii = it0 + b + hrow;
-              const int i = i_base + ii;
-              if (i < kp.p && r < kp.R)
-                epi.store((long long)i * kp.R + r, i, r, stg[ii * 33 + rr], stg[ii * 33 + 16 + rr], in[b]);
+              for (int b = 0; b < B; ++b) {
+                const int i = i_base + it0 + b + hrow;
+                if (i < kp.p && r < R32) epi.template load<1>((uint32_t)i * R32 + r, i, r, in[b]);
+              }
+#pragma unroll
+              for (int b = 0; b < B; ++b) {
+                const int ii = it0 + b + hrow;
+                const int i = i_base + ii;
+                if (i < kp.p && r < R32) {
+                  const float re[1] = {stg[ii * 33 + rr]}, im[1] = {stg[ii * 33 + 16 + rr]};
+                  epi.template store<1>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
+                }
+              }
             }
           }
           __syncwarp();

@@ -99,31 +99,52 @@ void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p)
 }
 
 // ------------------------------------------------------ standalone kernels
+// (P is a multiple of 8: every kernel handles 4 consecutive elements per step)
+
 // V = a u + b g(t, u) (split); optionally V2 = a2 u + b2 g(t, u) (split)
-__global__ void gsplit_kernel(long long P, b3::GStatic g, b3::GTime t, const float* __restrict__ U, float a, float b,
+__global__ void gsplit_kernel(uint32_t P, b3::GStatic g, b3::GTime t, const float* __restrict__ U, float a, float b,
                               SplitOut V, float a2, float b2, SplitOut V2) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P; q += (long long)gridDim.x * blockDim.x) {
-    const float ur = U[q], ui = U[P + q];
-    float gr = 0.f, gi = 0.f;
-    if (b != 0.f || (V2.hi && b2 != 0.f)) b3::g_eval(g, t, P, q, ur, ui, gr, gi);
-    b3::put_csplit(V, P, q, a * ur + b * gr, a * ui + b * gi);
-    if (V2.hi) b3::put_csplit(V2, P, q, a2 * ur + b2 * gr, a2 * ui + b2 * gi);
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    float ur[4], ui[4], gr[4] = {0, 0, 0, 0}, gi[4] = {0, 0, 0, 0}, xr[4], xi[4];
+    b3::ldv<4>(U + q, ur);
+    b3::ldv<4>(U + P + q, ui);
+    if (b != 0.f || (V2.hi && b2 != 0.f)) b3::g_eval<4>(g, t, P, q, ur, ui, gr, gi);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      xr[v] = a * ur[v] + b * gr[v];
+      xi[v] = a * ui[v] + b * gi[v];
+    }
+    b3::put_csplit<4>(V, P, q, xr, xi);
+    if (V2.hi) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        xr[v] = a2 * ur[v] + b2 * gr[v];
+        xi[v] = a2 * ui[v] + b2 * gi[v];
+      }
+      b3::put_csplit<4>(V2, P, q, xr, xi);
+    }
   }
 }
 
 // V = Phi_t(u) (split)
-__global__ void flow_split_kernel(long long P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P; q += (long long)gridDim.x * blockDim.x) {
-    float vr, vi;
-    b3::flow_eval(f, U[q], U[P + q], vr, vi);
-    b3::put_csplit(V, P, q, vr, vi);
+__global__ void flow_split_kernel(uint32_t P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    float ur[4], ui[4], vr[4], vi[4];
+    b3::ldv<4>(U + q, ur);
+    b3::ldv<4>(U + P + q, ui);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) b3::flow_eval(f, ur[v], ui[v], vr[v], vi[v]);
+    b3::put_csplit<4>(V, P, q, vr, vi);
   }
 }
 
-// split <-> FP32 (raw mode-product entry point)
-__global__ void to_split_kernel(long long n, const float* __restrict__ X, SplitOut Y) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-    b3::put_split(Y, q, X[q]);
+// FP32 -> split (raw mode-product entry point); n % 4 == 0
+__global__ void to_split_kernel(uint32_t n, const float* __restrict__ X, SplitOut Y) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < n; q += 4 * gridDim.x * blockDim.x) {
+    float x[4];
+    b3::ldv<4>(X + q, x);
+    b3::put_split<4>(Y, q, x);
+  }
 }
 
 int grid_for(long long n) {
@@ -148,6 +169,7 @@ class EngineB3 : public EngineBase {
       s_.N *= (size_t)s_.n[mu];
     }
     P_ = (long long)s_.P;
+    if (2 * s_.P >= (size_t(1) << 32)) throw Unsupported("BF16X3 handles need 2 P < 2^32 internal elements");
     for (int mu = 0; mu < prm.d; ++mu) {
       Direction D = spectral_direction(prm, mu);
       h_[mu] = D.h;
@@ -259,9 +281,9 @@ class EngineB3 : public EngineBase {
       store_split(xh, xh + 2 * s_.P, mu, fwd, out);
     } else {
       SplitOut t = SP(kT0);
-      to_split_kernel<<<grid_for(2 * P_), 256, 0, st_>>>(2 * P_, (const float*)X, t);
+      to_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), (const float*)X, t);
       FCGLE_LAUNCHED(launches);
-      launch_mp(t.hi, t.lo, mu, fwd, b3::EpiStoreF32{P_, (float*)Y});
+      launch_mp(t.hi, t.lo, mu, fwd, b3::EpiStoreF32{P32(), (float*)Y});
     }
   }
 
@@ -273,8 +295,8 @@ class EngineB3 : public EngineBase {
     SplitOut V = SP(kV);
     gsplit(X, 0.0, 1.f, 0.f, V);
     const float* Fp = Ften(func, k, theta);
-    tucker(V, true, b3::EpiScaleSplit{P_, Fp, V});
-    tucker(V, false, b3::EpiStoreF32{P_, X});
+    tucker(V, true, b3::EpiScaleSplit{P32(), Fp, V});
+    tucker(V, false, b3::EpiStoreF32{P32(), X});
     unpack_f32(X, (float*)out);
   }
 
@@ -326,6 +348,7 @@ class EngineB3 : public EngineBase {
   };
 
   float* F32(int i) { return f32_[i]->ptr; }
+  uint32_t P32() const { return (uint32_t)s_.P; }
   SplitOut SP(int i) { return SplitOut{sp_[i]->ptr, sp_[i]->ptr + 2 * s_.P}; }
 
   template <class Epi>
@@ -361,7 +384,7 @@ class EngineB3 : public EngineBase {
     if (R % 8 == 0)
       launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplit{}, &out);
     else
-      launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplitGen{P_, out});
+      launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplitGen{P32(), out});
   }
 
   // one mode product of direction mu on split input (xh, xl) with epilogue epi
@@ -428,7 +451,7 @@ class EngineB3 : public EngineBase {
   // V = a u + b g(t, u) (+ optional V2)
   void gsplit(const float* U, double t, float a, float b, SplitOut V, float a2 = 0.f, float b2 = 0.f,
               SplitOut V2 = SplitOut{}) {
-    gsplit_kernel<<<grid_for(P_), 256, 0, st_>>>(P_, gs_, gtime(t), U, a, b, V, a2, b2, V2);
+    gsplit_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), gs_, gtime(t), U, a, b, V, a2, b2, V2);
     FCGLE_LAUNCHED(launches);
   }
 
@@ -483,19 +506,19 @@ class EngineB3 : public EngineBase {
         const float* F = Ften(scheme == FCGLE_LIE ? FCGLE_F_INV : FCGLE_F_EXP, 0, tau);
         gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P_, F, V});
-          tucker(V, false, b3::EpiUpdateG{P_, U, 0, gs_, gtime(t0 + (n + 1) * tau), 1.f, ft, V});
+          tucker(V, true, b3::EpiScaleSplit{P32(), F, V});
+          tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t0 + (n + 1) * tau), 1.f, ft, V});
         }
         break;
       }
       case FCGLE_STRANG: {
         const float* E = Ften(FCGLE_F_EXP, 0, tau);
         const b3::Flow f = flow(tau / 2);
-        flow_split_kernel<<<grid_for(P_), 256, 0, st_>>>(P_, f, U, V);
+        flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), f, U, V);
         FCGLE_LAUNCHED(launches);
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P_, E, V});
-          tucker(V, false, b3::EpiStrang{P_, U, f, V});
+          tucker(V, true, b3::EpiScaleSplit{P32(), E, V});
+          tucker(V, false, b3::EpiStrang{P32(), U, f, V});
         }
         break;
       }
@@ -504,10 +527,10 @@ class EngineB3 : public EngineBase {
         float* EA = F32(kEA);
         gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P_, E, V});
-          tucker(V, false, b3::EpiStoreF32{P_, EA});
-          tucker(W, true, b3::EpiScaleSplit{P_, E, W});
-          tucker(W, false, b3::EpiLawsonRK2{P_, U, EA, gs_, gtime(t0 + (n + 1) * tau), ft, V, W});
+          tucker(V, true, b3::EpiScaleSplit{P32(), E, V});
+          tucker(V, false, b3::EpiStoreF32{P32(), EA});
+          tucker(W, true, b3::EpiScaleSplit{P32(), E, W});
+          tucker(W, false, b3::EpiLawsonRK2{P32(), U, EA, gs_, gtime(t0 + (n + 1) * tau), ft, V, W});
         }
         break;
       }
@@ -518,11 +541,11 @@ class EngineB3 : public EngineBase {
         // first step: linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps
         // u_0 as u_{n-1} and forms the first LBDF2 right-hand side
         gsplit(U, t0, 1.f, ft, V);
-        tucker(V, true, b3::EpiScaleSplit{P_, R1, V});
-        tucker(V, false, b3::EpiLBDF2{P_, U, Up, gs_, gtime(t0 + 2 * tau), ft, V});
+        tucker(V, true, b3::EpiScaleSplit{P32(), R1, V});
+        tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + 2 * tau), ft, V});
         for (int n = 1; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P_, R23, V});
-          tucker(V, false, b3::EpiLBDF2{P_, U, Up, gs_, gtime(t0 + (n + 2) * tau), ft, V});
+          tucker(V, true, b3::EpiScaleSplit{P32(), R23, V});
+          tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + (n + 2) * tau), ft, V});
         }
         break;
       }
@@ -531,18 +554,18 @@ class EngineB3 : public EngineBase {
         const float* P2 = Ften(FCGLE_F_PHI, 2, tau);
         float *Uh = F32(kUh), *Fh = F32(kFh);
         gsplit(U, t0, 1.f, 0.f, V);                              // U^_0 = fwd(u_0)
-        tucker(V, true, b3::EpiStoreF32{P_, Uh});
+        tucker(V, true, b3::EpiStoreF32{P32(), Uh});
         gsplit(U, t0, 0.f, 1.f, V);                              // G_0
         for (int n = 0; n < nsteps; ++n) {
           const double t = t0 + n * tau;
           // S1 = tau P1 o (Lam o U^ + G^);  a^ = U^ + S1
-          tucker(V, true, b3::EpiFhat{P_, lf_, Uh, Fh, P1, ft, 1, V});
+          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, P1, ft, 1, V});
           // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
-          tucker(V, false, b3::EpiStageD{P_, U, U, gs_, gtime(t + tau), gtime(t), V});
+          tucker(V, false, b3::EpiStageD{P32(), U, U, gs_, gtime(t + tau), gtime(t), V});
           // S2 = tau P2 o D^;  U^ += S2
-          tucker(V, true, b3::EpiStage2{P_, nullptr, nullptr, 0.f, P2, ft, nullptr, Uh, V});
+          tucker(V, true, b3::EpiStage2{P32(), nullptr, nullptr, 0.f, P2, ft, nullptr, Uh, V});
           // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
-          tucker(V, false, b3::EpiUpdateG{P_, U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
+          tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
         }
         break;
       }
@@ -554,25 +577,25 @@ class EngineB3 : public EngineBase {
         const float* P3 = Ften(FCGLE_F_PHI, 3, tau);
         float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *D3 = F32(kD3);
         gsplit(U, t0, 1.f, 0.f, V);
-        tucker(V, true, b3::EpiStoreF32{P_, Uh});
+        tucker(V, true, b3::EpiStoreF32{P32(), Uh});
         gsplit(U, t0, 0.f, 1.f, V);
         for (int n = 0; n < nsteps; ++n) {
           const double t = t0 + n * tau;
           const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
           // F^ = Lam o U^ + G^;  S = tau/2 P1(tau/2) F^
-          tucker(V, true, b3::EpiFhat{P_, lf_, Uh, Fh, P1h, 0.5f * ft, 0, V});
+          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, P1h, 0.5f * ft, 0, V});
           // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
-          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, th, tn, V});
+          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
           // D^_2;  S = tau (1/2 P1(tau/2) F^ + P2(tau/2) D^_2)
-          tucker(V, true, b3::EpiStage2{P_, Fh, P1h, 0.5f * ft, P2h, ft, D2, nullptr, V});
-          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, th, tn, V});
+          tucker(V, true, b3::EpiStage2{P32(), Fh, P1h, 0.5f * ft, P2h, ft, D2, nullptr, V});
+          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
           // D^_3;  S = tau (P1(tau) F^ + 2 P2(tau) D^_3)
-          tucker(V, true, b3::EpiStage2{P_, Fh, P1, ft, P2, 2.f * ft, D3, nullptr, V});
-          tucker(V, false, b3::EpiStageD{P_, U, nullptr, gs_, t1, tn, V});
+          tucker(V, true, b3::EpiStage2{P32(), Fh, P1, ft, P2, 2.f * ft, D3, nullptr, V});
+          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
           // D^_4;  final combination;  U^ += S
-          tucker(V, true, b3::EpiKrogFinal{P_, Fh, D2, D3, P1, P2, P3, Uh, ft, V});
+          tucker(V, true, b3::EpiKrogFinal{P32(), Fh, D2, D3, P1, P2, P3, Uh, ft, V});
           // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
-          tucker(V, false, b3::EpiUpdateG{P_, U, 1, gs_, t1, 0.f, 1.f, V});
+          tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, t1, 0.f, 1.f, V});
         }
         break;
       }
