@@ -157,6 +157,105 @@ __device__ __forceinline__ void cmulv(const float (&ar)[V], const float (&ai)[V]
   }
 }
 
+// ---------------------------------------------------- spectral scalars, FP32
+// phi_1, phi_2, phi_3 of z (Eq. phi).  |z| < 1.5: phi_3 by its power series
+// sum_m z^m/(m+3)! (13 terms, remainder < 1e-11 relative), then the exact
+// downward relations phi_2 = z phi_3 + 1/2, phi_1 = z phi_2 + 1, which involve
+// no cancellation.  |z| >= 1.5: e^z and the recurrence of Eq. phi.
+__device__ __forceinline__ void phi123(float zr, float zi, float (&pr)[3], float (&pi)[3]) {
+  if (zr * zr + zi * zi < 2.25f) {
+    // 1/(m+3)!, m = 0..12
+    constexpr float c[13] = {1.6666667e-01f, 4.1666668e-02f, 8.3333338e-03f, 1.3888889e-03f, 1.9841270e-04f,
+                             2.4801587e-05f, 2.7557319e-06f, 2.7557319e-07f, 2.5052108e-08f, 2.0876756e-09f,
+                             1.6059044e-10f, 1.1470746e-11f, 7.6471636e-13f};
+    float ar = c[12], ai = 0.f;
+#pragma unroll
+    for (int m = 11; m >= 0; --m) {
+      const float tr = ar * zr - ai * zi + c[m];
+      ai = ar * zi + ai * zr;
+      ar = tr;
+    }
+    pr[2] = ar;
+    pi[2] = ai;
+    pr[1] = zr * ar - zi * ai + 0.5f;
+    pi[1] = zr * ai + zi * ar;
+    pr[0] = zr * pr[1] - zi * pi[1] + 1.f;
+    pi[0] = zr * pi[1] + zi * pr[1];
+  } else {
+    float s, co;
+    sincosf(zi, &s, &co);
+    const float ex = expf(zr);
+    const float inv = 1.f / (zr * zr + zi * zi);
+    const float wr = zr * inv, wi = -zi * inv;   // 1/z
+    float er = ex * co - 1.f, ei = ex * s;       // e^z - 1
+    pr[0] = er * wr - ei * wi;
+    pi[0] = er * wi + ei * wr;
+    er = pr[0] - 1.f;
+    ei = pi[0];
+    pr[1] = er * wr - ei * wi;
+    pi[1] = er * wi + ei * wr;
+    er = pr[1] - 0.5f;
+    ei = pi[1];
+    pr[2] = er * wr - ei * wi;
+    pi[2] = er * wi + ei * wr;
+  }
+}
+
+// phi_k(z), any k >= 1: Horner form of the series
+// (1/k!)(1 + z/(k+1)(1 + z/(k+2)(...))) for |z| < 1.5, recurrence otherwise.
+__device__ __forceinline__ void phik(int k, float zr, float zi, float& fr, float& fi) {
+  if (zr * zr + zi * zi < 2.25f) {
+    float ar = 1.f, ai = 0.f;
+    for (int m = 16; m >= 1; --m) {
+      const float w = 1.f / (float)(m + k);
+      const float tr = 1.f + w * (ar * zr - ai * zi);
+      ai = w * (ar * zi + ai * zr);
+      ar = tr;
+    }
+    float f = 1.f;
+    for (int j = 2; j <= k; ++j) f *= (float)j;
+    fr = ar / f;
+    fi = ai / f;
+  } else {
+    float s, co;
+    sincosf(zi, &s, &co);
+    const float ex = expf(zr);
+    const float inv = 1.f / (zr * zr + zi * zi);
+    const float wr = zr * inv, wi = -zi * inv;
+    float pr = ex * co, pi = ex * s, fact = 1.f;
+    for (int l = 1; l <= k; ++l) {
+      if (l >= 2) fact /= (float)(l - 1);
+      const float er = pr - fact, ei = pi;
+      pr = er * wr - ei * wi;
+      pi = er * wi + ei * wr;
+    }
+    fr = pr;
+    fi = pi;
+  }
+}
+
+// f(z) for kind 0: 1/(1 - z), 1: e^z, 1 + l: phi_l (l >= 1)
+__device__ __forceinline__ void fspec(int kind, float zr, float zi, float& fr, float& fi) {
+  if (kind == 0) {
+    const float ar = 1.f - zr, ai = -zi, inv = 1.f / (ar * ar + ai * ai);
+    fr = ar * inv;
+    fi = -ai * inv;
+  } else if (kind == 1) {
+    float s, co;
+    sincosf(zi, &s, &co);
+    const float ex = expf(zr);
+    fr = ex * co;
+    fi = ex * s;
+  } else if (kind <= 4) {
+    float pr[3], pi[3];
+    phi123(zr, zi, pr, pi);
+    fr = pr[kind - 2];
+    fi = pi[kind - 2];
+  } else {
+    phik(kind - 1, zr, zi, fr, fi);
+  }
+}
+
 // ---------------------------------------------------------------- functors
 #define FCGLE_EPI(IN, BATCH)              \
   static constexpr bool kTmaStore = false; \
@@ -203,22 +302,28 @@ struct EpiStoreF32 {
   }
 };
 
-// Y = F o product  (split)
-struct EpiScaleSplit {
-  FCGLE_EPI(2, 2)
+// Y = f(theta lam) o product  (split), f evaluated on the fly (fspec kinds)
+struct EpiScaleF {
+  FCGLE_EPI(0, 4)
   uint32_t P;
-  const float* F;
+  LamF L;
+  int kind;
+  float theta;
   SplitOut Y;
   template <int V>
-  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
-    ldv_ro<V>(F + q, in[0]);
-    ldv_ro<V>(F + P + q, in[1]);
-  }
+  __device__ void load(uint32_t, int, uint32_t, float (&)[1][V]) const {}
   template <int V>
-  __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
-                        const float (&in)[2][V]) const {
-    float yr[V], yi[V];
-    cmulv<V>(in[0], in[1], re, im, yr, yi);
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&)[1][V]) const {
+    float lr[V], li[V], yr[V], yi[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float fr, fi;
+      fspec(kind, theta * lr[v], theta * li[v], fr, fi);
+      yr[v] = fr * re[v] - fi * im[v];
+      yi[v] = fr * im[v] + fi * re[v];
+    }
     put_csplit<V>(Y, P, q, yr, yi);
   }
 };
@@ -300,27 +405,26 @@ struct EpiStageD {
   }
 };
 
-// G^ = product;  F^ = Lam o U^ + G^ -> Fh;  S = c P1 o F^ -> split;  optionally U^ += S
+// G^ = product;  F^ = Lam o U^ + G^ -> Fh;  S = c phi_1(theta Lam) o F^ -> split;
+// optionally U^ += S
 struct EpiFhat {
-  FCGLE_EPI(4, 2)
+  FCGLE_EPI(2, 4)
   uint32_t P;
   LamF L;
   float* Uh;
   float* Fh;
-  const float* P1;
+  float theta;
   float c;
   int update_uh;
   SplitOut S;
   template <int V>
-  __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
     ldv<V>(Uh + q, in[0]);
     ldv<V>(Uh + P + q, in[1]);
-    ldv_ro<V>(P1 + q, in[2]);
-    ldv_ro<V>(P1 + P + q, in[3]);
   }
   template <int V>
   __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
-                        const float (&in)[4][V]) const {
+                        const float (&in)[2][V]) const {
     float lr[V], li[V], fr[V], fi[V], sr[V], si[V];
     lam_eval<V>(L, i, r, lr, li);
     cmulv<V>(lr, li, in[0], in[1], fr, fi);
@@ -328,15 +432,13 @@ struct EpiFhat {
     for (int v = 0; v < V; ++v) {
       fr[v] += re[v];
       fi[v] += im[v];
+      float pr[3], pi[3];
+      phi123(theta * lr[v], theta * li[v], pr, pi);
+      sr[v] = c * (pr[0] * fr[v] - pi[0] * fi[v]);
+      si[v] = c * (pr[0] * fi[v] + pi[0] * fr[v]);
     }
     stv<V>(Fh + q, fr);
     stv<V>(Fh + P + q, fi);
-    cmulv<V>(in[2], in[3], fr, fi, sr, si);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      sr[v] *= c;
-      si[v] *= c;
-    }
     put_csplit<V>(S, P, q, sr, si);
     if (update_uh) {
 #pragma unroll
@@ -350,109 +452,150 @@ struct EpiFhat {
   }
 };
 
-// D^ = product -> Dsave (optional);  S = a Pa o F^ + b Pb o D^ -> split;  optionally U^ += S
-struct EpiStage2 {
-  FCGLE_EPI(8, 1)
+// Krogstad stage 2 (Eq. krogstad-m), zh = tau/2 Lam:
+// D^_2 = product -> D2;  S = tau (1/2 phi_1(zh) F^ + phi_2(zh) D^_2) -> split
+struct EpiKrog2 {
+  FCGLE_EPI(2, 4)
   uint32_t P;
-  const float* Fh;   // may be null when a == 0
-  const float* Pa;
-  float a;
-  const float* Pb;
-  float b;
-  float* Dsave;
-  float* Uh;         // null: no update
-  SplitOut S;
-  template <int V>
-  __device__ void load(uint32_t q, int, uint32_t, float (&in)[8][V]) const {
-    ldv_ro<V>(Pb + q, in[0]);
-    ldv_ro<V>(Pb + P + q, in[1]);
-    if (a != 0.f) {
-      ldv_ro<V>(Pa + q, in[2]);
-      ldv_ro<V>(Pa + P + q, in[3]);
-      ldv_ro<V>(Fh + q, in[4]);
-      ldv_ro<V>(Fh + P + q, in[5]);
-    }
-    if (Uh) {
-      ldv<V>(Uh + q, in[6]);
-      ldv<V>(Uh + P + q, in[7]);
-    }
-  }
-  template <int V>
-  __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
-                        const float (&in)[8][V]) const {
-    if (Dsave) {
-      stv<V>(Dsave + q, re);
-      stv<V>(Dsave + P + q, im);
-    }
-    float sr[V], si[V], tr[V], ti[V];
-    cmulv<V>(in[0], in[1], re, im, sr, si);
-    if (a != 0.f) cmulv<V>(in[2], in[3], in[4], in[5], tr, ti);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      sr[v] *= b;
-      si[v] *= b;
-      if (a != 0.f) {
-        sr[v] += a * tr[v];
-        si[v] += a * ti[v];
-      }
-    }
-    put_csplit<V>(S, P, q, sr, si);
-    if (Uh) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        tr[v] = in[6][v] + sr[v];
-        ti[v] = in[7][v] + si[v];
-      }
-      stv<V>(Uh + q, tr);
-      stv<V>(Uh + P + q, ti);
-    }
-  }
-};
-
-// Krogstad's last combination (Eq. krogstad-m):
-// S = tau (P1 F^ + P2 (2 D2 + 2 D3 - D4) + P3 (-4 D2 - 4 D3 + 4 D4)) -> split; U^ += S
-struct EpiKrogFinal {
-  FCGLE_EPI(14, 1)
-  uint32_t P;
-  const float *Fh, *D2, *D3, *P1, *P2, *P3;
-  float* Uh;
+  LamF L;
+  const float* Fh;
+  float* D2;
   float tau;
   SplitOut S;
   template <int V>
-  __device__ void load(uint32_t q, int, uint32_t, float (&in)[14][V]) const {
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
+    ldv_ro<V>(Fh + q, in[0]);
+    ldv_ro<V>(Fh + P + q, in[1]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[2][V]) const {
+    stv<V>(D2 + q, re);
+    stv<V>(D2 + P + q, im);
+    float lr[V], li[V], sr[V], si[V];
+    lam_eval<V>(L, i, r, lr, li);
+    const float th = 0.5f * tau;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float pr[3], pi[3];
+      phi123(th * lr[v], th * li[v], pr, pi);
+      const float ar = 0.5f * (pr[0] * in[0][v] - pi[0] * in[1][v]) + (pr[1] * re[v] - pi[1] * im[v]);
+      const float ai = 0.5f * (pr[0] * in[1][v] + pi[0] * in[0][v]) + (pr[1] * im[v] + pi[1] * re[v]);
+      sr[v] = tau * ar;
+      si[v] = tau * ai;
+    }
+    put_csplit<V>(S, P, q, sr, si);
+  }
+};
+
+// Krogstad stage 3 (Eq. krogstad-m), z = tau Lam, D^_3 = product:
+// S = tau (phi_1 F^ + 2 phi_2 D^_3) -> split, and the part of the final
+// combination that is known now,
+// W = tau phi_1 F^ + (2 tau phi_2 - 4 tau phi_3) (D^_2 + D^_3) -> W (FP32),
+// since P2 (2 D2 + 2 D3 - D4) + P3 (-4 D2 - 4 D3 + 4 D4) = (2 P2 - 4 P3)(D2 + D3) + (4 P3 - P2) D4.
+struct EpiKrog3 {
+  FCGLE_EPI(4, 2)
+  uint32_t P;
+  LamF L;
+  const float* Fh;
+  const float* D2;
+  float* W;
+  float tau;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
     ldv_ro<V>(Fh + q, in[0]);
     ldv_ro<V>(Fh + P + q, in[1]);
     ldv_ro<V>(D2 + q, in[2]);
     ldv_ro<V>(D2 + P + q, in[3]);
-    ldv_ro<V>(D3 + q, in[4]);
-    ldv_ro<V>(D3 + P + q, in[5]);
-    ldv_ro<V>(P1 + q, in[6]);
-    ldv_ro<V>(P1 + P + q, in[7]);
-    ldv_ro<V>(P2 + q, in[8]);
-    ldv_ro<V>(P2 + P + q, in[9]);
-    ldv_ro<V>(P3 + q, in[10]);
-    ldv_ro<V>(P3 + P + q, in[11]);
-    ldv<V>(Uh + q, in[12]);
-    ldv<V>(Uh + P + q, in[13]);
   }
   template <int V>
-  __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
-                        const float (&in)[14][V]) const {
-    float sr[V], si[V], ur[V], ui[V];
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[4][V]) const {
+    float lr[V], li[V], sr[V], si[V], wr[V], wi[V];
+    lam_eval<V>(L, i, r, lr, li);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const float br = 2.f * in[2][v] + 2.f * in[4][v] - re[v], bi = 2.f * in[3][v] + 2.f * in[5][v] - im[v];
-      const float cr = 4.f * (re[v] - in[2][v] - in[4][v]), ci = 4.f * (im[v] - in[3][v] - in[5][v]);
-      float xr = in[6][v] * in[0][v] - in[7][v] * in[1][v];
-      float xi = in[6][v] * in[1][v] + in[7][v] * in[0][v];
-      xr += in[8][v] * br - in[9][v] * bi;
-      xi += in[8][v] * bi + in[9][v] * br;
-      xr += in[10][v] * cr - in[11][v] * ci;
-      xi += in[10][v] * ci + in[11][v] * cr;
-      sr[v] = tau * xr;
-      si[v] = tau * xi;
-      ur[v] = in[12][v] + sr[v];
-      ui[v] = in[13][v] + si[v];
+      float pr[3], pi[3];
+      phi123(tau * lr[v], tau * li[v], pr, pi);
+      const float fr = pr[0] * in[0][v] - pi[0] * in[1][v], fi = pr[0] * in[1][v] + pi[0] * in[0][v];
+      sr[v] = tau * (fr + 2.f * (pr[1] * re[v] - pi[1] * im[v]));
+      si[v] = tau * (fi + 2.f * (pr[1] * im[v] + pi[1] * re[v]));
+      const float er = in[2][v] + re[v], ei = in[3][v] + im[v];
+      const float cr = 2.f * pr[1] - 4.f * pr[2], ci = 2.f * pi[1] - 4.f * pi[2];
+      wr[v] = tau * (fr + cr * er - ci * ei);
+      wi[v] = tau * (fi + cr * ei + ci * er);
+    }
+    put_csplit<V>(S, P, q, sr, si);
+    stv<V>(W + q, wr);
+    stv<V>(W + P + q, wi);
+  }
+};
+
+// Krogstad final combination, D^_4 = product, z = tau Lam:
+// S = W + tau (4 phi_3 - phi_2) D^_4 -> split;  U^ += S
+struct EpiKrogFinal {
+  FCGLE_EPI(4, 2)
+  uint32_t P;
+  LamF L;
+  const float* W;
+  float* Uh;
+  float tau;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
+    ldv_ro<V>(W + q, in[0]);
+    ldv_ro<V>(W + P + q, in[1]);
+    ldv<V>(Uh + q, in[2]);
+    ldv<V>(Uh + P + q, in[3]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[4][V]) const {
+    float lr[V], li[V], sr[V], si[V], ur[V], ui[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float pr[3], pi[3];
+      phi123(tau * lr[v], tau * li[v], pr, pi);
+      const float cr = tau * (4.f * pr[2] - pr[1]), ci = tau * (4.f * pi[2] - pi[1]);
+      sr[v] = in[0][v] + cr * re[v] - ci * im[v];
+      si[v] = in[1][v] + cr * im[v] + ci * re[v];
+      ur[v] = in[2][v] + sr[v];
+      ui[v] = in[3][v] + si[v];
+    }
+    put_csplit<V>(S, P, q, sr, si);
+    stv<V>(Uh + q, ur);
+    stv<V>(Uh + P + q, ui);
+  }
+};
+
+// ETD2RK second stage, D^ = product, z = tau Lam: S = tau phi_2(z) D^ -> split;  U^ += S
+struct EpiEtd2 {
+  FCGLE_EPI(2, 4)
+  uint32_t P;
+  LamF L;
+  float* Uh;
+  float tau;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
+    ldv<V>(Uh + q, in[0]);
+    ldv<V>(Uh + P + q, in[1]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[2][V]) const {
+    float lr[V], li[V], sr[V], si[V], ur[V], ui[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float pr[3], pi[3];
+      phi123(tau * lr[v], tau * li[v], pr, pi);
+      sr[v] = tau * (pr[1] * re[v] - pi[1] * im[v]);
+      si[v] = tau * (pr[1] * im[v] + pi[1] * re[v]);
+      ur[v] = in[0][v] + sr[v];
+      ui[v] = in[1][v] + si[v];
     }
     put_csplit<V>(S, P, q, sr, si);
     stv<V>(Uh + q, ur);

@@ -45,12 +45,6 @@ struct DevMem {
   DevMem& operator=(const DevMem&) = delete;
 };
 
-uint64_t bits_of(double x) {
-  uint64_t u;
-  std::memcpy(&u, &x, 8);
-  return u;
-}
-
 int num_sms() {
   static int sms = 0;
   if (!sms) {
@@ -173,15 +167,9 @@ class EngineB3 : public EngineBase {
     for (int mu = 0; mu < prm.d; ++mu) {
       Direction D = spectral_direction(prm, mu);
       h_[mu] = D.h;
-      std::vector<double> lp(s_.p[mu], 0.0);
       std::vector<float> lf(s_.p[mu], 0.f);
-      for (int j = 0; j < D.n; ++j) {
-        lp[j] = D.lam[j];
-        lf[j] = (float)D.lam[j];
-      }
-      lam_[mu].reset(new DevMem<double>(s_.p[mu]));
+      for (int j = 0; j < D.n; ++j) lf[j] = (float)D.lam[j];
       lamf_[mu].reset(new DevMem<float>(s_.p[mu]));
-      FCGLE_CUDA(cudaMemcpy(lam_[mu]->ptr, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice));
       FCGLE_CUDA(cudaMemcpy(lamf_[mu]->ptr, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
       const int p = s_.p[mu];
       std::vector<double> Mf((size_t)p * p, 0.0), Mb((size_t)p * p, 0.0);
@@ -193,9 +181,6 @@ class EngineB3 : public EngineBase {
       prepare_matrix(Mf.data(), p, mat_[mu][0]);
       prepare_matrix(Mb.data(), p, mat_[mu][1]);
     }
-    lv_.c_re = prm.nu;
-    lv_.c_im = prm.eta;
-    for (int mu = 0; mu < kMaxDim; ++mu) lv_.lam[mu] = mu < prm.d ? lam_[mu]->ptr : nullptr;
     lf_.d = prm.d;
     lf_.c_re = (float)prm.nu;
     lf_.c_im = (float)prm.eta;
@@ -224,12 +209,14 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiStoreSplit>();
       set_smem_attr<b3::EpiStoreSplitGen>();
       set_smem_attr<b3::EpiStoreF32>();
-      set_smem_attr<b3::EpiScaleSplit>();
+      set_smem_attr<b3::EpiScaleF>();
       set_smem_attr<b3::EpiUpdateG>();
       set_smem_attr<b3::EpiStageD>();
       set_smem_attr<b3::EpiFhat>();
-      set_smem_attr<b3::EpiStage2>();
+      set_smem_attr<b3::EpiKrog2>();
+      set_smem_attr<b3::EpiKrog3>();
       set_smem_attr<b3::EpiKrogFinal>();
+      set_smem_attr<b3::EpiEtd2>();
       set_smem_attr<b3::EpiLBDF2>();
       set_smem_attr<b3::EpiLawsonRK2>();
       set_smem_attr<b3::EpiStrang>();
@@ -294,8 +281,7 @@ class EngineB3 : public EngineBase {
     pack_f32((const float*)v, X);
     SplitOut V = SP(kV);
     gsplit(X, 0.0, 1.f, 0.f, V);
-    const float* Fp = Ften(func, k, theta);
-    tucker(V, true, b3::EpiScaleSplit{P32(), Fp, V});
+    tucker(V, true, b3::EpiScaleF{P32(), lf_, fkind(func, k), (float)theta, V});
     tucker(V, false, b3::EpiStoreF32{P32(), X});
     unpack_f32(X, (float*)out);
   }
@@ -465,37 +451,16 @@ class EngineB3 : public EngineBase {
     return f;
   }
 
-  const float* Ften(int func, int ell, double theta) {
-    if (func == FCGLE_F_PHI && ell == 0) func = FCGLE_F_EXP;
-    if (func != FCGLE_F_PHI) ell = 0;
-    auto key = std::make_tuple(func, ell, bits_of(theta));
-    auto it = fcache_.find(key);
-    if (it != fcache_.end()) return it->second->ptr;
-    auto* b = new DevMem<float>(2 * s_.P);
-    fcache_[key].reset(b);
-    fill_F<float>(s_, lv_, func, ell, theta, b->ptr, st_, launches);
-    return b->ptr;
-  }
-
-  void prepare(int scheme, double tau) {
-    switch (scheme) {
-      case FCGLE_LIE: Ften(FCGLE_F_INV, 0, tau); break;
-      case FCGLE_LBDF2: Ften(FCGLE_F_INV, 0, tau); Ften(FCGLE_F_INV, 0, 2.0 * tau / 3.0); break;
-      case FCGLE_LAWSON_EULER:
-      case FCGLE_LAWSON_RK2:
-      case FCGLE_STRANG: Ften(FCGLE_F_EXP, 0, tau); break;
-      case FCGLE_ETD2RK: Ften(FCGLE_F_PHI, 1, tau); Ften(FCGLE_F_PHI, 2, tau); break;
-      case FCGLE_KROGSTAD:
-        Ften(FCGLE_F_PHI, 1, tau / 2); Ften(FCGLE_F_PHI, 2, tau / 2);
-        Ften(FCGLE_F_PHI, 1, tau); Ften(FCGLE_F_PHI, 2, tau); Ften(FCGLE_F_PHI, 3, tau);
-        break;
-      default: throw InvalidArg("unknown scheme");
-    }
+  // spectral scalar f(theta lam), evaluated on the fly by the epilogues (b3 fspec kinds)
+  static int fkind(int func, int k) {
+    if (func == FCGLE_F_INV) return 0;
+    if (func == FCGLE_F_EXP || k == 0) return 1;
+    return 1 + k;
   }
 
   // prologue (entry state of the loop), then nsteps fused steps on F32(kU)
   void run(int scheme, double tau, int nsteps, double t0) {
-    prepare(scheme, tau);
+    if (scheme < FCGLE_LIE || scheme > FCGLE_STRANG) throw InvalidArg("unknown scheme");
     if (nsteps == 0) return;
     float* U = F32(kU);
     SplitOut V = SP(kV), W = SP(kW);
@@ -503,97 +468,87 @@ class EngineB3 : public EngineBase {
     switch (scheme) {
       case FCGLE_LIE:
       case FCGLE_LAWSON_EULER: {
-        const float* F = Ften(scheme == FCGLE_LIE ? FCGLE_F_INV : FCGLE_F_EXP, 0, tau);
+        const int kind = scheme == FCGLE_LIE ? 0 : 1;   // (1 - tau lam)^{-1} or e^{tau lam}
         gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P32(), F, V});
+          tucker(V, true, b3::EpiScaleF{P32(), lf_, kind, ft, V});
           tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t0 + (n + 1) * tau), 1.f, ft, V});
         }
         break;
       }
       case FCGLE_STRANG: {
-        const float* E = Ften(FCGLE_F_EXP, 0, tau);
         const b3::Flow f = flow(tau / 2);
         flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), f, U, V);
         FCGLE_LAUNCHED(launches);
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P32(), E, V});
+          tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
           tucker(V, false, b3::EpiStrang{P32(), U, f, V});
         }
         break;
       }
       case FCGLE_LAWSON_RK2: {
-        const float* E = Ften(FCGLE_F_EXP, 0, tau);
         float* EA = F32(kEA);
         gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
         for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P32(), E, V});
+          tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
           tucker(V, false, b3::EpiStoreF32{P32(), EA});
-          tucker(W, true, b3::EpiScaleSplit{P32(), E, W});
+          tucker(W, true, b3::EpiScaleF{P32(), lf_, 1, ft, W});
           tucker(W, false, b3::EpiLawsonRK2{P32(), U, EA, gs_, gtime(t0 + (n + 1) * tau), ft, V, W});
         }
         break;
       }
       case FCGLE_LBDF2: {
-        const float* R1 = Ften(FCGLE_F_INV, 0, tau);
-        const float* R23 = Ften(FCGLE_F_INV, 0, 2.0 * tau / 3.0);
         float* Up = F32(kUp);
+        const float t23 = (float)(2.0 * tau / 3.0);
         // first step: linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps
         // u_0 as u_{n-1} and forms the first LBDF2 right-hand side
         gsplit(U, t0, 1.f, ft, V);
-        tucker(V, true, b3::EpiScaleSplit{P32(), R1, V});
+        tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, ft, V});
         tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + 2 * tau), ft, V});
         for (int n = 1; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleSplit{P32(), R23, V});
+          tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, t23, V});
           tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + (n + 2) * tau), ft, V});
         }
         break;
       }
       case FCGLE_ETD2RK: {
-        const float* P1 = Ften(FCGLE_F_PHI, 1, tau);
-        const float* P2 = Ften(FCGLE_F_PHI, 2, tau);
         float *Uh = F32(kUh), *Fh = F32(kFh);
         gsplit(U, t0, 1.f, 0.f, V);                              // U^_0 = fwd(u_0)
         tucker(V, true, b3::EpiStoreF32{P32(), Uh});
         gsplit(U, t0, 0.f, 1.f, V);                              // G_0
         for (int n = 0; n < nsteps; ++n) {
           const double t = t0 + n * tau;
-          // S1 = tau P1 o (Lam o U^ + G^);  a^ = U^ + S1
-          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, P1, ft, 1, V});
+          // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
+          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V});
           // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
           tucker(V, false, b3::EpiStageD{P32(), U, U, gs_, gtime(t + tau), gtime(t), V});
-          // S2 = tau P2 o D^;  U^ += S2
-          tucker(V, true, b3::EpiStage2{P32(), nullptr, nullptr, 0.f, P2, ft, nullptr, Uh, V});
+          // S2 = tau phi_2(tau Lam) o D^;  U^ += S2
+          tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V});
           // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
           tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
         }
         break;
       }
       case FCGLE_KROGSTAD: {
-        const float* P1h = Ften(FCGLE_F_PHI, 1, tau / 2);
-        const float* P2h = Ften(FCGLE_F_PHI, 2, tau / 2);
-        const float* P1 = Ften(FCGLE_F_PHI, 1, tau);
-        const float* P2 = Ften(FCGLE_F_PHI, 2, tau);
-        const float* P3 = Ften(FCGLE_F_PHI, 3, tau);
-        float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *D3 = F32(kD3);
+        float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *Wc = F32(kD3);
         gsplit(U, t0, 1.f, 0.f, V);
         tucker(V, true, b3::EpiStoreF32{P32(), Uh});
         gsplit(U, t0, 0.f, 1.f, V);
         for (int n = 0; n < nsteps; ++n) {
           const double t = t0 + n * tau;
           const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
-          // F^ = Lam o U^ + G^;  S = tau/2 P1(tau/2) F^
-          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, P1h, 0.5f * ft, 0, V});
+          // F^ = Lam o U^ + G^;  S = tau/2 phi_1(tau/2 Lam) F^
+          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, 0.5f * ft, 0.5f * ft, 0, V});
           // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
           tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
-          // D^_2;  S = tau (1/2 P1(tau/2) F^ + P2(tau/2) D^_2)
-          tucker(V, true, b3::EpiStage2{P32(), Fh, P1h, 0.5f * ft, P2h, ft, D2, nullptr, V});
+          // D^_2;  S = tau (1/2 phi_1(tau/2 Lam) F^ + phi_2(tau/2 Lam) D^_2)
+          tucker(V, true, b3::EpiKrog2{P32(), lf_, Fh, D2, ft, V});
           tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
-          // D^_3;  S = tau (P1(tau) F^ + 2 P2(tau) D^_3)
-          tucker(V, true, b3::EpiStage2{P32(), Fh, P1, ft, P2, 2.f * ft, D3, nullptr, V});
+          // D^_3;  S = tau (phi_1 F^ + 2 phi_2 D^_3);  W = part of the final combination
+          tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V});
           tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
-          // D^_4;  final combination;  U^ += S
-          tucker(V, true, b3::EpiKrogFinal{P32(), Fh, D2, D3, P1, P2, P3, Uh, ft, V});
+          // D^_4;  S = W + tau (4 phi_3 - phi_2) D^_4;  U^ += S
+          tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V});
           // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
           tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, t1, 0.f, 1.f, V});
         }
@@ -609,9 +564,7 @@ class EngineB3 : public EngineBase {
   long long P_ = 0;
   double h_[kMaxDim] = {1, 1, 1};
   Mat mat_[kMaxDim][2];
-  std::unique_ptr<DevMem<double>> lam_[kMaxDim];
   std::unique_ptr<DevMem<float>> lamf_[kMaxDim];
-  LamVecs lv_{};
   b3::LamF lf_{};
   b3::GStatic gs_{};
   double sig_re_[kMaxSrc] = {0, 0, 0, 0}, sig_im_[kMaxSrc] = {0, 0, 0, 0};
@@ -621,7 +574,6 @@ class EngineB3 : public EngineBase {
   std::unique_ptr<DevMem<float>> host_stage_;
   std::unique_ptr<DevMem<double>> scratch_;
   std::unique_ptr<DevMem<int>> err_;
-  std::map<std::tuple<int, int, uint64_t>, std::unique_ptr<DevMem<float>>> fcache_;
 };
 
 std::unique_ptr<EngineBase> make_engine_b3(const fcgle_params& prm, cudaStream_t st) {
