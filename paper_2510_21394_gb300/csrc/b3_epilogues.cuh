@@ -262,20 +262,11 @@ __device__ __forceinline__ void fspec(int kind, float zr, float zi, float& fr, f
   static constexpr int kIn = IN;           \
   static constexpr int kBatch = BATCH;
 
-// FP32 planar operands the epilogue will read (prefetched into L2 ahead of it)
-#define FCGLE_PF0 \
-  __device__ int pf_ptrs(const float* (&)[4]) const { return 0; }
-#define FCGLE_PF1(A) \
-  __device__ int pf_ptrs(const float* (&p)[4]) const { p[0] = (A); return p[0] ? 1 : 0; }
-#define FCGLE_PF2(A, B) \
-  __device__ int pf_ptrs(const float* (&p)[4]) const { p[0] = A; p[1] = B; return 2; }
-
 // product -> split, through TMA stores
 struct EpiStoreSplit {
   static constexpr bool kTmaStore = true;
   static constexpr int kIn = 0;
   static constexpr int kBatch = 1;
-  FCGLE_PF0
   template <int V>
   __device__ void load(uint32_t, int, uint32_t, float (&)[1][V]) const {}
   template <int V>
@@ -285,7 +276,6 @@ struct EpiStoreSplit {
 // product -> split, element stores (any R)
 struct EpiStoreSplitGen {
   FCGLE_EPI(0, 4)
-  FCGLE_PF0
   uint32_t P;
   SplitOut Y;
   template <int V>
@@ -300,7 +290,6 @@ struct EpiStoreSplitGen {
 // product -> FP32
 struct EpiStoreF32 {
   FCGLE_EPI(0, 4)
-  FCGLE_PF0
   uint32_t P;
   float* Y;
   template <int V>
@@ -316,7 +305,6 @@ struct EpiStoreF32 {
 // Y = f(theta lam) o product  (split), f evaluated on the fly (fspec kinds)
 struct EpiScaleF {
   FCGLE_EPI(0, 4)
-  FCGLE_PF0
   uint32_t P;
   LamF L;
   int kind;
@@ -343,7 +331,6 @@ struct EpiScaleF {
 // u = (add ? U : 0) + product -> U (FP32);  V = a u + b g(t', u) -> split
 struct EpiUpdateG {
   FCGLE_EPI(2, 2)
-  FCGLE_PF1(add ? U : static_cast<float*>(nullptr))
   uint32_t P;
   float* U;
   int add;
@@ -383,7 +370,6 @@ struct EpiUpdateG {
 // u_s = U + product;  D = g(t_s, u_s) - g(t_n, U) -> split;  optionally U_out = u_s
 struct EpiStageD {
   FCGLE_EPI(2, 2)
-  FCGLE_PF1(U)
   uint32_t P;
   const float* U;
   float* Uout;
@@ -423,7 +409,6 @@ struct EpiStageD {
 // optionally U^ += S
 struct EpiFhat {
   FCGLE_EPI(2, 4)
-  FCGLE_PF1(Uh)
   uint32_t P;
   LamF L;
   float* Uh;
@@ -471,7 +456,6 @@ struct EpiFhat {
 // D^_2 = product -> D2;  S = tau (1/2 phi_1(zh) F^ + phi_2(zh) D^_2) -> split
 struct EpiKrog2 {
   FCGLE_EPI(2, 4)
-  FCGLE_PF1(Fh)
   uint32_t P;
   LamF L;
   const float* Fh;
@@ -511,7 +495,6 @@ struct EpiKrog2 {
 // since P2 (2 D2 + 2 D3 - D4) + P3 (-4 D2 - 4 D3 + 4 D4) = (2 P2 - 4 P3)(D2 + D3) + (4 P3 - P2) D4.
 struct EpiKrog3 {
   FCGLE_EPI(4, 2)
-  FCGLE_PF2(Fh, D2)
   uint32_t P;
   LamF L;
   const float* Fh;
@@ -553,7 +536,6 @@ struct EpiKrog3 {
 // S = W + tau (4 phi_3 - phi_2) D^_4 -> split;  U^ += S
 struct EpiKrogFinal {
   FCGLE_EPI(4, 2)
-  FCGLE_PF2(W, Uh)
   uint32_t P;
   LamF L;
   const float* W;
@@ -591,7 +573,6 @@ struct EpiKrogFinal {
 // ETD2RK second stage, D^ = product, z = tau Lam: S = tau phi_2(z) D^ -> split;  U^ += S
 struct EpiEtd2 {
   FCGLE_EPI(2, 4)
-  FCGLE_PF1(Uh)
   uint32_t P;
   LamF L;
   float* Uh;
@@ -626,7 +607,6 @@ struct EpiEtd2 {
 // next right-hand side 4/3 u_{n+1} - 1/3 u_n + 2 tau/3 g(t_{n+2}, 2 u_{n+1} - u_n) -> split
 struct EpiLBDF2 {
   FCGLE_EPI(2, 2)
-  FCGLE_PF1(U)
   uint32_t P;
   float* U;
   float* Uprev;
@@ -667,7 +647,6 @@ struct EpiLBDF2 {
 // next k1 = g(t_{n+1}, u_{n+1}); A = u + tau k1, B = u + tau/2 k1 -> split
 struct EpiLawsonRK2 {
   FCGLE_EPI(2, 2)
-  FCGLE_PF1(EA)
   uint32_t P;
   float* U;
   const float* EA;
@@ -725,7 +704,6 @@ __device__ __forceinline__ void flow_eval(const Flow& f, float wr, float wi, flo
 // Strang (Eq. Strang): u_{n+1} = Phi(product) -> U;  next V = Phi(u_{n+1}) -> split
 struct EpiStrang {
   FCGLE_EPI(0, 4)
-  FCGLE_PF0
   uint32_t P;
   float* U;
   Flow f;
@@ -748,9 +726,6 @@ struct EpiStrang {
 };
 
 #undef FCGLE_EPI
-#undef FCGLE_PF0
-#undef FCGLE_PF1
-#undef FCGLE_PF2
 
 }  // namespace b3
 }  // namespace fcgle

@@ -58,7 +58,6 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
 
 struct KParams {
   long long R;      // rows per plane of X; row length of the output planes
-  long long P;      // plane size of the epilogue's standard-order operands (p * R)
   int p;            // extent of the contracted / produced index (rows of M)
   int m_blocks;     // ceil(p / 128)
   int k_chunks;     // ceil(p / 64)
@@ -118,9 +117,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
-}
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   // K-major, SWIZZLE_128B: rows of 128 bytes, 8-row groups 1024 bytes apart.
@@ -223,17 +219,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    // lane 0 issues the TMA loads of a unit; lanes 1..31 then prefetch into
-    // L2 the rows of the epilogue's FP32 operands for that unit (its
-    // epilogue runs one or two units later).
-    uint32_t g = 0;
-    bool ok = true;
-    const float* pf[4];
-    const int npf = epi.pf_ptrs(pf);
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-      const long long tile = u / kp.m_blocks;
-      const int mb = (int)(u % kp.m_blocks);
-      if (lane == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const long long tile = u / kp.m_blocks;
+        const int mb = (int)(u % kp.m_blocks);
         const int r0 = (int)(tile * BR);
         const int r1 = (int)(kp.R + tile * BR);   // same r in the imaginary plane
         for (int kc = 0; kc < KC; ++kc, ++g) {
@@ -250,21 +241,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tma_load_2d(st + 49152 + 8192, &tm_xlo, kc * BK, r1, full_bar(s));
         }
       }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) break;
-      if (npf > 0 && lane > 0 && (kp.R & 3) == 0) {
-        const long long r0 = tile * BR;
-        const uint32_t bytes = (uint32_t)(min((long long)BR, kp.R - r0) * 4);
-        const int rows = min(BM, kp.p - mb * BM);
-        const int jobs = npf * 2 * rows;
-        for (int j = lane - 1; j < jobs; j += 31) {
-          const int op = j / (2 * rows), rem = j % (2 * rows), c = rem / rows, ii = rem % rows;
-          prefetch_l2(pf[op] + (long long)c * kp.P + (long long)(mb * BM + ii) * kp.R + r0, bytes);
-        }
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
       // drain: every issued stage must have landed before the CTA may exit
       const uint32_t issued = g;
       for (uint32_t q = issued >= NSTAGE ? issued - NSTAGE : 0; q < issued; ++q)

@@ -384,7 +384,6 @@ class EngineB3 : public EngineBase {
     encode_bf16(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
     b3::KParams kp;
     kp.R = R;
-    kp.P = P_;
     kp.p = s_.p[mu];
     kp.m_blocks = m.m_pad / b3::BM;
     kp.k_chunks = m.k_pad / b3::BK;
