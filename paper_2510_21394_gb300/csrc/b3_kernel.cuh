@@ -287,55 +287,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;            // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;  // which two of the four 16-column groups
     float* stg = reinterpret_cast<float*>(smem + kOffEpi + (warp - 2) * kEpiWarp);
-    constexpr int NI = Epi::kIn > 0 ? Epi::kIn : 1;
-    // operands of the functor for one 16-column group: 4 row groups x NI x 4 r
-    // (quad path).  Functors with few operands keep both column groups in
-    // registers so all loads of a unit are in flight before the accumulator
-    // is ready; the others prefetch the first group only.
-    constexpr int NSET = (Epi::kTmaStore || NI > 2) ? 1 : 2;
-    const uint32_t R32 = (uint32_t)kp.R;
-    const bool quad = (R32 & 3u) == 0;
-    const int k4 = lane & 3, a8 = lane >> 2;
-    float in[NSET][4][NI][4];
-    auto issue_loads = [&](float (&dst)[4][NI][4], long long tile, int i_base, int cc) {
-      const uint32_t r = (uint32_t)(tile * BR + cc * 16 + 4 * k4);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = i_base + a8 + 8 * b;
-        if (i < kp.p && r < R32) epi.template load<4>((uint32_t)i * R32 + r, i, r, dst[b]);
-      }
-    };
-    auto compute_stores = [&](const float (&src)[4][NI][4], long long tile, int i_base, int cc) {
-      const uint32_t r = (uint32_t)(tile * BR + cc * 16 + 4 * k4);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int ii = a8 + 8 * b;
-        const int i = i_base + ii;
-        if (i < kp.p && r < R32) {
-          float re[4], im[4];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            re[v] = stg[ii * 33 + 4 * k4 + v];
-            im[v] = stg[ii * 33 + 16 + 4 * k4 + v];
-          }
-          epi.template store<4>((uint32_t)i * R32 + r, i, r, re, im, src[b]);
-        }
-      }
-    };
+    const int rr = lane & 15, hrow = (lane >> 4) * 16;
     uint32_t t = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++t) {
       const int a = t & 1;
+      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, kp.err, 9)) break;
+      tc_fence_after();
       const long long tile = u / kp.m_blocks;
       const int mb = (int)(u % kp.m_blocks);
       const int i_base = mb * BM + q * 32;
-      if constexpr (!Epi::kTmaStore) {
-        if (quad) {
-          issue_loads(in[0], tile, i_base, half);
-          if constexpr (NSET == 2) issue_loads(in[NSET - 1], tile, i_base, half + 2);
-        }
-      }
-      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, kp.err, 9)) break;
-      tc_fence_after();
 #pragma unroll 1
       for (int g2 = 0; g2 < 2; ++g2) {
         const int cc = half + 2 * g2;   // 16-column group: r = r0 + 16 cc + 0..15
@@ -384,25 +344,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
           }
           __syncwarp();
-          if (quad) {
-            // lane = 4 a + k: rows a, a + 8, a + 16, a + 24 and r = 16 cc + 4 k + 0..3
-            if constexpr (NSET == 2) {
-              compute_stores(in[g2], tile, i_base, cc);
-            } else {
-              if (g2 == 1) issue_loads(in[0], tile, i_base, cc);
-              compute_stores(in[0], tile, i_base, cc);
+          constexpr int B = Epi::kBatch;
+          constexpr int NI = Epi::kIn > 0 ? Epi::kIn : 1;
+          const uint32_t R32 = (uint32_t)kp.R;
+          if ((R32 & 3u) == 0) {
+            // 4 consecutive r per lane: lane = 4 a + k covers rows a, a + 8, .. and r = 16 cc + 4 k + 0..3
+            const int k4 = lane & 3, a8 = lane >> 2;
+            const uint32_t r = (uint32_t)(tile * BR + cc * 16 + 4 * k4);
+#pragma unroll 1
+            for (int it0 = 0; it0 < 4; it0 += B) {
+              float in[B][NI][4];
+#pragma unroll
+              for (int b = 0; b < B; ++b) {
+                const int i = i_base + a8 + 8 * (it0 + b);
+                if (i < kp.p && r < R32) epi.template load<4>((uint32_t)i * R32 + r, i, r, in[b]);
+              }
+#pragma unroll
+              for (int b = 0; b < B; ++b) {
+                const int ii = a8 + 8 * (it0 + b);
+                const int i = i_base + ii;
+                if (i < kp.p && r < R32) {
+                  float re[4], im[4];
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) {
+                    re[v] = stg[ii * 33 + 4 * k4 + v];
+                    im[v] = stg[ii * 33 + 16 + 4 * k4 + v];
+                  }
+                  epi.template store<4>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
+                }
+              }
             }
           } else {
-            constexpr int B = Epi::kBatch;
-            const int rr = lane & 15, hrow = (lane >> 4) * 16;
             const uint32_t r = (uint32_t)(tile * BR + cc * 16 + rr);
 #pragma unroll 1
             for (int it0 = 0; it0 < 16; it0 += B) {
-              float in1[B][NI][1];
+              float in[B][NI][1];
 #pragma unroll
               for (int b = 0; b < B; ++b) {
                 const int i = i_base + it0 + b + hrow;
-                if (i < kp.p && r < R32) epi.template load<1>((uint32_t)i * R32 + r, i, r, in1[b]);
+                if (i < kp.p && r < R32) epi.template load<1>((uint32_t)i * R32 + r, i, r, in[b]);
               }
 #pragma unroll
               for (int b = 0; b < B; ++b) {
@@ -410,7 +390,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int i = i_base + ii;
                 if (i < kp.p && r < R32) {
                   const float re[1] = {stg[ii * 33 + rr]}, im[1] = {stg[ii * 33 + 16 + rr]};
-                  epi.template store<1>((uint32_t)i * R32 + r, i, r, re, im, in1[b]);
+                  epi.template store<1>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
                 }
               }
             }
