@@ -120,6 +120,13 @@ fcgle_status fcgle_set_stream(fcgle_handle h, void* cuda_stream);
 fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_reim,
                               const void* const* S_dev);
 
+/* Replaces nu, eta, gamma, kappa, zeta of the handle (same validity rules as
+ * fcgle_setup).  Cheap: D_mu and its eigendecomposition depend only on the
+ * grid and alpha_mu; cached spectral tensors are dropped.  Synchronises the
+ * handle's stream first (FP64 handles). */
+fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, double gamma, double kappa,
+                                    double zeta);
+
 /* out = f(theta K) v with f = 1/(1-z) (func INV), e^z (EXP, Eq. Neudeckerd)
  * or phi_k (PHI, k in 0..4).  v and out are device tensors in the user layout
  * and may alias. */
@@ -139,6 +146,21 @@ fcgle_status fcgle_integrate(fcgle_handle h, int scheme, double tau, int nsteps,
  * copies the result device -> host and synchronises the stream. */
 fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int nsteps, double t0,
                                   const void* u0_host, void* uT_host);
+
+/* Gradient of the final-time misfit J = 1/2 sum_j |u_j(T) - u_target,j|^2
+ * (T = t0 + nsteps tau, no cell volume) with respect to the initial state and
+ * the parameters, by the discrete adjoint of the scheme (only
+ * FCGLE_LAWSON_RK2; others give FCGLE_ERR_UNSUPPORTED).  Gradients are in the
+ * real sense: grad_u0 = dJ/dRe u0 + i dJ/dIm u0 (device tensor, user layout);
+ * grad_params[5] (host) = dJ/d(nu, eta, gamma, kappa, zeta); *loss (host) = J.
+ * States are checkpointed every ckpt_every steps (0: one segment) and each
+ * segment is recomputed once, so the cost is about three forward runs and
+ * the extra device memory (5 ckpt_every + nsteps / ckpt_every + 9) tensors.
+ * Synchronises the stream.  The exponential is applied in the Tucker form
+ * (Eq. fKu_diag with f = exp). */
+fcgle_status fcgle_adjoint(fcgle_handle h, int scheme, double tau, int nsteps, double t0, const void* u0,
+                           const void* u_target, int ckpt_every, void* grad_u0, double* grad_params,
+                           double* loss);
 
 /* Discrete L2 norm (prod_mu h_mu sum_j |u_j|^2)^{1/2} (Sec. 4) of a device
  * tensor, written to *out_host (synchronises the stream). */

@@ -1,0 +1,238 @@
+// Pointwise kernels and reductions of the discrete adjoint (adjoint.h).
+// Planar internal layout (common.h); FP64 accumulation of every reduction
+// (warp shuffles, one atomic per block and slot).
+#include <cmath>
+
+#include "adjoint.h"
+
+namespace fcgle {
+
+namespace {
+
+int grid_of(size_t n) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 132;
+  }
+  size_t g = (n + 255) / 256;
+  if (g > (size_t)sms * 8) g = (size_t)sms * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// block-reduce NV values and atomically add them to acc[slot0 + k]
+template <int NV>
+__device__ void block_acc(double (&v)[NV], double* acc, int slot0) {
+  __shared__ double red[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? red[k][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) atomicAdd(acc + slot0 + k, x);
+    }
+  }
+}
+
+// g source term sum_k e^{sigma_k t} S_k is independent of u: its derivative vanishes.
+struct GP {
+  double gamma, kappa, zeta;
+};
+
+template <typename T>
+__global__ void misfit_kernel(size_t P, const T* __restrict__ u, const T* __restrict__ tg, T* __restrict__ lam,
+                              double* acc) {
+  double v[1] = {0.0};
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    const double dr = (double)u[q] - (double)tg[q], di = (double)u[P + q] - (double)tg[P + q];
+    lam[q] = (T)dr;
+    lam[P + q] = (T)di;
+    v[0] += 0.5 * (dr * dr + di * di);
+  }
+  block_acc<1>(v, acc, ADJ_LOSS);
+}
+
+// (D_z g)^* w = conj(alpha) w + beta conj(w),  alpha = gamma - 2 c |z|^2, beta = -c z^2, c = kappa + i zeta
+__device__ __forceinline__ void gadj(const GP& g, double zr, double zi, double wr, double wi, double& orr,
+                                     double& oi) {
+  const double m2 = zr * zr + zi * zi;
+  const double ar = g.gamma - 2.0 * g.kappa * m2, ai = -2.0 * g.zeta * m2;   // alpha
+  const double z2r = zr * zr - zi * zi, z2i = 2.0 * zr * zi;
+  const double br = -(g.kappa * z2r - g.zeta * z2i), bi = -(g.kappa * z2i + g.zeta * z2r);   // beta
+  // conj(alpha) w + beta conj(w)
+  orr = ar * wr + ai * wi + br * wr + bi * wi;
+  oi = ar * wi - ai * wr + bi * wr - br * wi;
+}
+// Re<w, dg/dp(z)> for p = gamma, kappa, zeta
+__device__ __forceinline__ void gpar(double zr, double zi, double wr, double wi, double (&v)[3]) {
+  const double m2 = zr * zr + zi * zi;
+  v[0] += wr * zr + wi * zi;                 // Re(conj(w) z)
+  v[1] += -m2 * (wr * zr + wi * zi);         // Re(conj(w) (-|z|^2 z))
+  v[2] += -m2 * (wr * (-zi) + wi * zr);      // Re(conj(w) (-i |z|^2 z)),  -i z = (zi, -zr) * (-1)
+}
+
+template <typename T>
+__global__ void gv_kernel(size_t P, GP g, const T* __restrict__ z, const T* __restrict__ w, double c,
+                          T* __restrict__ mu, double* acc) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    const double zr = z[q], zi = z[P + q], wr = c * (double)w[q], wi = c * (double)w[P + q];
+    double orr, oi;
+    gadj(g, zr, zi, wr, wi, orr, oi);
+    mu[q] = (T)orr;
+    mu[P + q] = (T)oi;
+    gpar(zr, zi, wr, wi, v);
+  }
+  block_acc<3>(v, acc, ADJ_GAMMA);
+}
+
+template <typename T>
+__global__ void gu_kernel(size_t P, GP g, const T* __restrict__ u, const T* __restrict__ la,
+                          const T* __restrict__ lb, double ca, double cb, T* __restrict__ out, double* acc) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    const double ar = la[q], ai = la[P + q], br = lb[q], bi = lb[P + q];
+    const double kr = ca * ar + cb * br, ki = ca * ai + cb * bi;
+    const double zr = u[q], zi = u[P + q];
+    double orr, oi;
+    gadj(g, zr, zi, kr, ki, orr, oi);
+    out[q] = (T)(ar + br + orr);
+    out[P + q] = (T)(ai + bi + oi);
+    gpar(zr, zi, kr, ki, v);
+  }
+  block_acc<3>(v, acc, ADJ_GAMMA);
+}
+
+struct LD {
+  const double* lam[kMaxDim];
+  int p[kMaxDim];
+  int n[kMaxDim];
+  int d;
+};
+__device__ __forceinline__ bool lam_sum(const LD& L, size_t q, double& s) {
+  s = 0.0;
+  bool valid = true;
+  size_t rem = q;
+  for (int mu = 0; mu < L.d; ++mu) {
+    const int j = (int)(rem % L.p[mu]);
+    rem /= L.p[mu];
+    valid = valid && j < L.n[mu];
+    s += L.lam[mu][j];
+  }
+  return valid;
+}
+
+template <typename T>
+__global__ void scale_exp_kernel(size_t P, LD L, double cre, double cim, const T* __restrict__ x, T* __restrict__ y) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    double s;
+    const bool valid = lam_sum(L, q, s);
+    double er = 0.0, ei = 0.0;
+    if (valid) {
+      double sn, cs;
+      sincos(cim * s, &sn, &cs);
+      const double m = exp(cre * s);
+      er = m * cs;
+      ei = m * sn;
+    }
+    const double xr = x[q], xi = x[P + q];
+    y[q] = (T)(er * xr - ei * xi);
+    y[P + q] = (T)(er * xi + ei * xr);
+  }
+}
+
+template <typename T>
+__global__ void spec_dot_kernel(size_t P, LD L, const T* __restrict__ x, const T* __restrict__ y, double* acc) {
+  double v[2] = {0.0, 0.0};
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    double s;
+    if (!lam_sum(L, q, s)) continue;
+    const double xr = x[q], xi = x[P + q], yr = y[q], yi = y[P + q];
+    v[0] += s * (xr * yr + xi * yi);   // Re conj(x) y
+    v[1] += s * (xr * yi - xi * yr);   // Im conj(x) y
+  }
+  block_acc<2>(v, acc, ADJ_Z_RE);
+}
+
+template <typename T>
+__global__ void axpby_kernel(size_t n, double a, const T* __restrict__ x1, double b, const T* __restrict__ x2,
+                             T* __restrict__ y) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    y[q] = (T)(a * (double)x1[q] + (x2 ? b * (double)x2[q] : 0.0));
+}
+
+LD make_ld(const Shape& s, const LamVecs& lv) {
+  LD L;
+  for (int mu = 0; mu < kMaxDim; ++mu) {
+    L.lam[mu] = lv.lam[mu];
+    L.p[mu] = s.p[mu];
+    L.n[mu] = s.n[mu];
+  }
+  L.d = s.d;
+  return L;
+}
+
+}  // namespace
+
+template <typename T>
+void adj_misfit(const Shape& s, const T* u, const T* target, T* lam, double* acc, cudaStream_t st, long long& nl) {
+  misfit_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, u, target, lam, acc);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_gv(const Shape& s, const GParams& gp, const T* z, const T* w, double c, T* mu, double* acc, cudaStream_t st,
+            long long& nl) {
+  gv_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, c, mu, acc);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_gu(const Shape& s, const GParams& gp, const T* u, const T* la, const T* lb, double ca, double cb, T* out,
+            double* acc, cudaStream_t st, long long& nl) {
+  gu_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, GP{gp.gamma, gp.kappa, gp.zeta}, u, la, lb, ca, cb, out, acc);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_scale_exp(const Shape& s, const LamVecs& lv, double theta, bool conj, const T* x, T* y, cudaStream_t st,
+                   long long& nl) {
+  scale_exp_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re,
+                                                      (conj ? -1.0 : 1.0) * theta * lv.c_im, x, y);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, double* acc, cudaStream_t st,
+                  long long& nl) {
+  spec_dot_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), x, y, acc);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* y, cudaStream_t st, long long& nl) {
+  axpby_kernel<T><<<grid_of(2 * s.P), 256, 0, st>>>(2 * s.P, a, x1, b, x2, y);
+  FCGLE_LAUNCHED(nl);
+}
+
+#define INST(T)                                                                                                  \
+  template void adj_misfit<T>(const Shape&, const T*, const T*, T*, double*, cudaStream_t, long long&);          \
+  template void adj_gv<T>(const Shape&, const GParams&, const T*, const T*, double, T*, double*, cudaStream_t,  \
+                          long long&);                                                                          \
+  template void adj_gu<T>(const Shape&, const GParams&, const T*, const T*, const T*, double, double, T*,       \
+                          double*, cudaStream_t, long long&);                                                   \
+  template void adj_scale_exp<T>(const Shape&, const LamVecs&, double, bool, const T*, T*, cudaStream_t,        \
+                                 long long&);                                                                   \
+  template void adj_spec_dot<T>(const Shape&, const LamVecs&, const T*, const T*, double*, cudaStream_t,        \
+                                long long&);                                                                    \
+  template void adj_axpby<T>(const Shape&, double, const T*, double, const T*, T*, cudaStream_t, long long&);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace fcgle

@@ -129,6 +129,23 @@ fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_re
   });
 }
 
+fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, double gamma, double kappa,
+                                    double zeta) {
+  return guarded([&] {
+    check_handle(h);
+    if (!(nu > 0.0)) throw InvalidArg("nu must be positive");
+    if (!(kappa > 0.0)) throw InvalidArg("kappa must be positive");
+    if (!std::isfinite(eta) || !std::isfinite(gamma) || !std::isfinite(zeta))
+      throw InvalidArg("eta, gamma, zeta must be finite");
+    h->eng->set_coefficients(nu, eta, gamma, kappa, zeta);
+    h->prm.nu = nu;
+    h->prm.eta = eta;
+    h->prm.gamma = gamma;
+    h->prm.kappa = kappa;
+    h->prm.zeta = zeta;
+  });
+}
+
 fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta, const void* v, void* out) {
   return guarded([&] {
     check_handle(h);
@@ -174,6 +191,19 @@ fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int ns
     h->eng->integrate_host(scheme, tau, nsteps, t0, u0_host, uT_host);
     if (int code = h->eng->device_error())
       throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
+  });
+}
+
+fcgle_status fcgle_adjoint(fcgle_handle h, int scheme, double tau, int nsteps, double t0, const void* u0,
+                           const void* u_target, int ckpt_every, void* grad_u0, double* grad_params, double* loss) {
+  return guarded([&] {
+    check_handle(h);
+    check_scheme(scheme);
+    check_tau(tau);
+    if (nsteps < 0) throw InvalidArg("nsteps must be >= 0");
+    if (ckpt_every < 0) throw InvalidArg("ckpt_every must be >= 0");
+    if (!u0 || !u_target || !grad_u0 || !grad_params || !loss) throw InvalidArg("pointer is NULL");
+    h->eng->adjoint(scheme, tau, nsteps, t0, u0, u_target, ckpt_every, grad_u0, grad_params, loss);
   });
 }
 

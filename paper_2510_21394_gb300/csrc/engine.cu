@@ -16,6 +16,7 @@
 #include <cstring>
 #include <cstdint>
 
+#include "adjoint.h"
 #include "engine.h"
 
 namespace fcgle {
@@ -175,6 +176,22 @@ class Engine : public EngineBase {
     gp_.nsrc = nterms;
   }
 
+  void set_coefficients(double nu, double eta, double gamma, double kappa, double zeta) override {
+    FCGLE_CUDA(cudaStreamSynchronize(st_));   // cached tensors may still be in use
+    prm_.nu = nu;
+    prm_.eta = eta;
+    prm_.gamma = gamma;
+    prm_.kappa = kappa;
+    prm_.zeta = zeta;
+    lv_.c_re = nu;
+    lv_.c_im = eta;
+    gp_.gamma = gamma;
+    gp_.kappa = kappa;
+    gp_.zeta = zeta;
+    fcache_.clear();
+    ecache_.clear();
+  }
+
   int device_error() override {
     int h = 0;
     FCGLE_CUDA(cudaStreamSynchronize(st_));
@@ -224,6 +241,38 @@ class Engine : public EngineBase {
     unpack<T>(s_, B(kU), host_stage_->ptr, st_, launches);
     FCGLE_CUDA(cudaMemcpyAsync(uT, host_stage_->ptr, bytes, cudaMemcpyDeviceToHost, st_));
     FCGLE_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  // ---- adjoint support (adjoint.h driver interface)
+  Shape shape() const { return s_; }
+  cudaStream_t stream() const { return st_; }
+  long long& nlaunch() { return launches; }
+  GParams gparams() const { return gp_; }
+  LamVecs lamvecs() const { return lv_; }
+  T* alloc(size_t n) {
+    adj_mem_.emplace_back(new DevBuf<T>(n));
+    return adj_mem_.back()->ptr;
+  }
+  void release_all() { adj_mem_.clear(); }
+  void tuckerT(const T* X, T* Y, bool fwd) { tucker(X, Y, fwd); }
+
+  void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
+               void* grad_u0, double* grad_params, double* loss) override {
+    if (scheme != FCGLE_LAWSON_RK2) throw Unsupported("the adjoint is implemented for LAWSON_RK2");
+    try {
+      T* U0 = alloc(2 * s_.P);
+      T* TG = alloc(2 * s_.P);
+      T* GR = alloc(2 * s_.P);
+      pack<T>(s_, (const T*)u0, U0, st_, launches);
+      pack<T>(s_, (const T*)target, TG, st_, launches);
+      adjoint_lawson_rk2<T>(*this, tau, nsteps, t0, U0, TG, ckpt, GR, grad_params, loss);
+      unpack<T>(s_, GR, (T*)grad_u0, st_, launches);
+      FCGLE_CUDA(cudaStreamSynchronize(st_));
+    } catch (...) {
+      release_all();
+      throw;
+    }
+    release_all();
   }
 
   double norm(const void* u) override {
@@ -574,6 +623,7 @@ class Engine : public EngineBase {
   std::unique_ptr<DevBuf<int>> err_;
   std::map<std::tuple<int, int, uint64_t>, std::unique_ptr<DevBuf<T>>> fcache_;
   std::map<uint64_t, std::vector<std::unique_ptr<DevBuf<double>>>> ecache_;
+  std::vector<std::unique_ptr<DevBuf<T>>> adj_mem_;
 };
 
 Direction spectral_direction(const fcgle_params& prm, int mu) {

@@ -39,11 +39,16 @@ class EngineBase {
   virtual ~EngineBase() = default;
   virtual void set_stream(cudaStream_t st) = 0;
   virtual void set_source(int nterms, const double* sig, const void* const* S_user) = 0;
+  // new nu, eta, gamma, kappa, zeta (the eigendecompositions do not depend on them)
+  virtual void set_coefficients(double nu, double eta, double gamma, double kappa, double zeta) = 0;
   virtual void apply_f(int func, int k, double theta, const void* v, void* out) = 0;
   virtual void step(int scheme, double tau, double t, void* u) = 0;
   virtual void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
   virtual void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
   virtual double norm(const void* u) = 0;
+  // discrete adjoint of Lawson-RK2 (adjoint.h); user-layout device tensors, synchronous
+  virtual void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target,
+                       int ckpt_every, void* grad_u0, double* grad_params, double* loss) = 0;
   virtual void mode_product(int mu, bool fwd, const void* X, void* Y) = 0;
   // flags: bit 0 forward (Q^T), bit 1 split-bf16 input and output (BF16X3 only)
   virtual void mode_product_flags(int mu, int flags, const void* X, void* Y) {

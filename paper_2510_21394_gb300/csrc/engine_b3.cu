@@ -23,6 +23,7 @@
 #include <tuple>
 #include <vector>
 
+#include "adjoint.h"
 #include "b3_epilogues.cuh"
 #include "b3_kernel.cuh"
 #include "engine.h"
@@ -168,9 +169,15 @@ class EngineB3 : public EngineBase {
       Direction D = spectral_direction(prm, mu);
       h_[mu] = D.h;
       std::vector<float> lf(s_.p[mu], 0.f);
-      for (int j = 0; j < D.n; ++j) lf[j] = (float)D.lam[j];
+      std::vector<double> ld(s_.p[mu], 0.0);
+      for (int j = 0; j < D.n; ++j) {
+        lf[j] = (float)D.lam[j];
+        ld[j] = D.lam[j];
+      }
       lamf_[mu].reset(new DevMem<float>(s_.p[mu]));
+      lamd_[mu].reset(new DevMem<double>(s_.p[mu]));
       FCGLE_CUDA(cudaMemcpy(lamf_[mu]->ptr, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+      FCGLE_CUDA(cudaMemcpy(lamd_[mu]->ptr, ld.data(), ld.size() * 8, cudaMemcpyHostToDevice));
       const int p = s_.p[mu];
       std::vector<double> Mf((size_t)p * p, 0.0), Mb((size_t)p * p, 0.0);
       for (int i = 0; i < D.n; ++i)
@@ -248,6 +255,19 @@ class EngineB3 : public EngineBase {
     gs_.nsrc = nterms;
   }
 
+  void set_coefficients(double nu, double eta, double gamma, double kappa, double zeta) override {
+    prm_.nu = nu;
+    prm_.eta = eta;
+    prm_.gamma = gamma;
+    prm_.kappa = kappa;
+    prm_.zeta = zeta;
+    lf_.c_re = (float)nu;
+    lf_.c_im = (float)eta;
+    gs_.gamma = (float)gamma;
+    gs_.kappa = (float)kappa;
+    gs_.zeta = (float)zeta;
+  }
+
   int device_error() override {
     int h = 0;
     FCGLE_CUDA(cudaStreamSynchronize(st_));
@@ -308,6 +328,61 @@ class EngineB3 : public EngineBase {
     unpack_f32(F32(kU), host_stage_->ptr);
     FCGLE_CUDA(cudaMemcpyAsync(uT, host_stage_->ptr, bytes, cudaMemcpyDeviceToHost, st_));
     FCGLE_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  // ---- adjoint support (adjoint.h driver interface): generic FP32 planar Tucker operators
+  Shape shape() const { return s_; }
+  cudaStream_t stream() const { return st_; }
+  long long& nlaunch() { return launches; }
+  GParams gparams() const {
+    GParams g;
+    g.gamma = prm_.gamma;
+    g.kappa = prm_.kappa;
+    g.zeta = prm_.zeta;
+    g.nsrc = gs_.nsrc;
+    for (int k = 0; k < kMaxSrc; ++k) {
+      g.sig_re[k] = sig_re_[k];
+      g.sig_im[k] = sig_im_[k];
+      g.S[k] = gs_.S[k];
+    }
+    return g;
+  }
+  LamVecs lamvecs() const {
+    LamVecs lv;
+    lv.c_re = prm_.nu;
+    lv.c_im = prm_.eta;
+    for (int mu = 0; mu < kMaxDim; ++mu) lv.lam[mu] = mu < s_.d ? lamd_[mu]->ptr : nullptr;
+    return lv;
+  }
+  float* alloc(size_t n) {
+    adj_mem_.emplace_back(new DevMem<float>(n));
+    return adj_mem_.back()->ptr;
+  }
+  void release_all() { adj_mem_.clear(); }
+  void tuckerT(const float* X, float* Y, bool fwd) {
+    SplitOut V = SP(kV);
+    to_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), X, V);
+    FCGLE_LAUNCHED(launches);
+    tucker(V, fwd, b3::EpiStoreF32{P32(), Y});
+  }
+
+  void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
+               void* grad_u0, double* grad_params, double* loss) override {
+    if (scheme != FCGLE_LAWSON_RK2) throw Unsupported("the adjoint is implemented for LAWSON_RK2");
+    try {
+      float* U0 = alloc(2 * s_.P);
+      float* TG = alloc(2 * s_.P);
+      float* GR = alloc(2 * s_.P);
+      pack_f32((const float*)u0, U0);
+      pack_f32((const float*)target, TG);
+      adjoint_lawson_rk2<float>(*this, tau, nsteps, t0, U0, TG, ckpt, GR, grad_params, loss);
+      unpack_f32(GR, (float*)grad_u0);
+      FCGLE_CUDA(cudaStreamSynchronize(st_));
+    } catch (...) {
+      release_all();
+      throw;
+    }
+    release_all();
   }
 
   double norm(const void* u) override {
@@ -565,6 +640,8 @@ class EngineB3 : public EngineBase {
   double h_[kMaxDim] = {1, 1, 1};
   Mat mat_[kMaxDim][2];
   std::unique_ptr<DevMem<float>> lamf_[kMaxDim];
+  std::unique_ptr<DevMem<double>> lamd_[kMaxDim];
+  std::vector<std::unique_ptr<DevMem<float>>> adj_mem_;
   b3::LamF lf_{};
   b3::GStatic gs_{};
   double sig_re_[kMaxSrc] = {0, 0, 0, 0}, sig_im_[kMaxSrc] = {0, 0, 0, 0};

@@ -39,7 +39,7 @@ PRECISIONS = {"fp64": FCGLE_FP64, "bf16x3": FCGLE_BF16X3}
 EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f", "fcgle_step",
            "fcgle_integrate", "fcgle_integrate_host", "fcgle_norm", "fcgle_sync", "fcgle_sizes",
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
-           "fcgle_internal_elems", "fcgle_mode_product"]
+           "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -79,6 +79,8 @@ def _load():
         "fcgle_destroy": [H],
         "fcgle_internal_elems": [H, ctypes.POINTER(ctypes.c_size_t)],
         "fcgle_mode_product": [H, I, I, P, P],
+        "fcgle_adjoint": [H, I, D, I, D, P, P, I, P, ctypes.POINTER(D), ctypes.POINTER(D)],
+        "fcgle_set_coefficients": [H, D, D, D, D, D],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -150,6 +152,10 @@ def fcgle_set_source(h, sigmas, tensors):
     _check(_lib.fcgle_set_source(h, n, sig, ptrs))
 
 
+def fcgle_set_coefficients(h, nu, eta, gamma, kappa, zeta):
+    _check(_lib.fcgle_set_coefficients(h, float(nu), float(eta), float(gamma), float(kappa), float(zeta)))
+
+
 def fcgle_apply_f(h, func, k, theta, v, out):
     func = FUNCS[func] if isinstance(func, str) else int(func)
     _check(_lib.fcgle_apply_f(h, func, int(k), float(theta), _ptr(v), _ptr(out)))
@@ -168,6 +174,16 @@ def fcgle_integrate(h, scheme, tau, nsteps, t0, u0, uT):
 def fcgle_integrate_host(h, scheme, tau, nsteps, t0, u0, uT):
     scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     _check(_lib.fcgle_integrate_host(h, scheme, float(tau), int(nsteps), float(t0), _ptr(u0), _ptr(uT)))
+
+
+def fcgle_adjoint(h, scheme, tau, nsteps, t0, u0, u_target, ckpt_every, grad_u0):
+    """Returns (loss, [dJ/dnu, dJ/deta, dJ/dgamma, dJ/dkappa, dJ/dzeta]); grad_u0 is written."""
+    scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    gp = (ctypes.c_double * 5)()
+    loss = ctypes.c_double()
+    _check(_lib.fcgle_adjoint(h, scheme, float(tau), int(nsteps), float(t0), _ptr(u0), _ptr(u_target),
+                              int(ckpt_every), _ptr(grad_u0), gp, ctypes.byref(loss)))
+    return loss.value, list(gp)
 
 
 def fcgle_norm(h, u):
@@ -250,6 +266,9 @@ class Solver:
         tensors = [self._check_tensor(t.contiguous()) for t in tensors]
         fcgle_set_source(self.h, sigmas, tensors)
 
+    def set_coefficients(self, nu, eta, gamma, kappa, zeta):
+        fcgle_set_coefficients(self.h, nu, eta, gamma, kappa, zeta)
+
     def apply_f(self, func, k, theta, v, out=None):
         v = self._check_tensor(v.contiguous())
         out = torch.empty_like(v) if out is None else out
@@ -269,6 +288,14 @@ class Solver:
     def integrate_host(self, scheme, tau, nsteps, u0_host, out_host, t0=0.0):
         fcgle_integrate_host(self.h, scheme, tau, nsteps, t0, u0_host, out_host)
         return out_host
+
+    def adjoint(self, scheme, tau, nsteps, u0, u_target, ckpt_every=25, t0=0.0):
+        """(loss, grad_u0, grad_params) of J = 1/2 ||u(T) - u_target||^2."""
+        u0 = self._check_tensor(u0.contiguous())
+        u_target = self._check_tensor(u_target.contiguous())
+        g = torch.empty_like(u0)
+        loss, gp = fcgle_adjoint(self.h, scheme, tau, nsteps, t0, u0, u_target, ckpt_every, g)
+        return loss, g, gp
 
     def norm(self, u):
         return fcgle_norm(self.h, self._check_tensor(u))
