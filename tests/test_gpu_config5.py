@@ -1,0 +1,61 @@
+"""Adjoint workload at full size: 3D 128^3, alpha = (1.5, 1.5, 1.5), Lawson-RK2,
+tau = 2e-3, 250 steps, checkpoints every 25; target from a forward run with
+the parameters scaled by 1.05.  The FP64 gradient is checked by central
+differences of the FP64 GPU forward map; the split-BF16 gradient against the
+FP64 one."""
+import numpy as np
+import pytest
+
+from paper_2510_21394_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NS = [128, 128, 128]
+BOXES = [(-10.0, 10.0)] * 3
+AL = [1.5, 1.5, 1.5]
+PARS = [1.0, 0.5, 1.0, 1.0, 0.5]
+TAU, M, CK = 2e-3, 250, 25
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_21394_gb300 import fcgle
+    return fcgle
+
+
+def test_config5_gradients(fc):
+    u0 = inputs.gaussian_random_phase(NS, BOXES, seed=3)
+    s64 = fc.Solver(NS, BOXES, AL, *PARS, precision="fp64")
+    v0 = torch.from_numpy(u0).cuda()
+    s64.set_coefficients(*[1.05 * x for x in PARS])
+    target = s64.integrate("lawson_rk2", TAU, M, v0)
+    s64.set_coefficients(*PARS)
+    loss, g64, gp64 = s64.adjoint("lawson_rk2", TAU, M, v0, target, ckpt_every=CK)
+    assert loss > 0 and np.all(np.isfinite(gp64))
+
+    def J(pars):
+        s64.set_coefficients(*pars)
+        uT = s64.integrate("lawson_rk2", TAU, M, v0)
+        s64.set_coefficients(*PARS)
+        return 0.5 * float(torch.sum(torch.abs(uT - target) ** 2))
+    for k in (1, 3):   # eta (through exp(tau K)) and kappa (through g)
+        h = 1e-5 * max(1.0, abs(PARS[k]))
+        pp, pm = list(PARS), list(PARS)
+        pp[k] += h
+        pm[k] -= h
+        fd = (J(pp) - J(pm)) / (2 * h)
+        assert gp64[k] == pytest.approx(fd, rel=1e-5), (k, gp64[k], fd)
+
+    s32 = fc.Solver(NS, BOXES, AL, *PARS, precision="bf16x3")
+    loss32, g32, gp32 = s32.adjoint("lawson_rk2", TAU, M, v0.to(torch.complex64), target.to(torch.complex64),
+                                    ckpt_every=CK)
+    rel_u = float(torch.linalg.vector_norm(g32.to(torch.complex128) - g64) / torch.linalg.vector_norm(g64))
+    rel_p = float(np.max(np.abs(np.array(gp32) - np.array(gp64)) / np.abs(np.array(gp64))))
+    print(f"config5: J = {loss:.6e}; bf16x3 vs fp64: grad_u0 rel {rel_u:.2e}, params max rel {rel_p:.2e}")
+    assert loss32 == pytest.approx(loss, rel=1e-3)
+    assert rel_u < 1e-2 and rel_p < 1e-2
+    s64.close()
+    s32.close()
