@@ -12,20 +12,20 @@
 // combinations of a scheme and write any outputs, split or FP32.
 //
 // GEMM orientation: D[i][col] = sum_k A[i][k] B[col][k] with A = M (MMA M =
-// 128 output indices i per block) and B = 2 BR data rows: the same BR = 128
-// indices r0..r0+127 of the real plane (columns 0..127) and of the imaginary
-// plane (columns 128..255), so each epilogue thread sees complete complex values.
+// 128 output indices i per block) and B = 128 data rows: the same 64 indices
+// r0..r0+63 of the real plane (columns 0..63) and of the imaginary plane
+// (columns 64..127), so each epilogue thread sees complete complex values.
 //
 // Warp roles (10 warps, one CTA per SM, persistent over (r-tile, i-block)):
-//   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x BR x 64)
+//   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x 64 x 64)
 //               bf16 chunks, SWIZZLE_128B, straight into the MMA layout.
 //   warp 1      TMEM allocator and single-thread MMA issuer (3 MMAs per k-step).
 //   warps 2-9   epilogue: TMEM -> registers, then either split + TMA bulk
 //               tensor stores of 32 x 16 boxes (plain mode products), or an
 //               smem transpose and a functor on coalesced (i, r) runs.  Warp w
-//               reads TMEM lane quarter w % 4 and the 16-column groups
-//               (w - 2) / 4 + 2 j of each plane.
-// Pipelines: 2 smem stages (96 KB each), 2 TMEM accumulators (2 x 256 columns).
+//               reads TMEM lane quarter w % 4 and column groups (w - 2) / 4 and
+//               (w - 2) / 4 + 2.
+// Pipelines: 3 smem stages (64 KB each), 2 TMEM accumulators (2 x 128 columns).
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error code in *err, drains its own TMA and MMA work, frees its
 // TMEM and returns.
@@ -40,20 +40,14 @@ namespace fcgle {
 namespace b3 {
 
 constexpr int BM = 128;     // output indices i per MMA
-constexpr int BR = 128;     // r indices per tile (x 2 planes = MMA N)
+constexpr int BR = 64;      // r indices per tile (x 2 planes = MMA N)
 constexpr int BN = 2 * BR;  // MMA N
 constexpr int BK = 64;      // k per chunk (one 128-byte bf16 row)
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int NEPI = 8;     // epilogue warps
 constexpr int NTHREADS = 32 * (2 + NEPI);
 
-constexpr uint32_t kMBytes = BM * 128;           // one 128 x 64 bf16 chunk of M
-constexpr uint32_t kXPlane = BR * 128;           // one plane's BR x 64 bf16 rows of X
-constexpr uint32_t kOffMlo = kMBytes;
-constexpr uint32_t kOffXhi = 2 * kMBytes;
-constexpr uint32_t kOffXlo = kOffXhi + 2 * kXPlane;
-constexpr uint32_t kStage = kOffXlo + 2 * kXPlane;   // M_hi | M_lo | X_hi (re, im) | X_lo (re, im)
-constexpr int NGROUP = BR / 16;                      // 16-column groups per plane
+constexpr uint32_t kStage = 65536;   // M_hi 16K | M_lo 16K | X_hi 16K | X_lo 16K
 constexpr uint32_t kOffEpi = NSTAGE * kStage;
 constexpr uint32_t kEpiWarp = 32 * 33 * 4;
 constexpr uint32_t kOffBar = kOffEpi + NEPI * kEpiWarp;
@@ -240,11 +234,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t st = sbase + s * kStage;
           mbar_arrive_tx(full_bar(s), kStage);
           tma_load_2d(st, &tm_mhi, kc * BK, mb * BM, full_bar(s));
-          tma_load_2d(st + kOffMlo, &tm_mlo, kc * BK, mb * BM, full_bar(s));
-          tma_load_2d(st + kOffXhi, &tm_xhi, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + kOffXhi + kXPlane, &tm_xhi, kc * BK, r1, full_bar(s));
-          tma_load_2d(st + kOffXlo, &tm_xlo, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + kOffXlo + kXPlane, &tm_xlo, kc * BK, r1, full_bar(s));
+          tma_load_2d(st + 16384, &tm_mlo, kc * BK, mb * BM, full_bar(s));
+          tma_load_2d(st + 32768, &tm_xhi, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 32768 + 8192, &tm_xhi, kc * BK, r1, full_bar(s));
+          tma_load_2d(st + 49152, &tm_xlo, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 49152 + 8192, &tm_xlo, kc * BK, r1, full_bar(s));
         }
       }
       // drain: every issued stage must have landed before the CTA may exit
@@ -269,8 +263,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t ph = (g / NSTAGE) & 1;
           if (!mbar_wait(full_bar(s), ph, abort_flag, kp.err, 3)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ahi = sbase + s * kStage, alo = ahi + kOffMlo;
-          const uint32_t bhi = ahi + kOffXhi, blo = ahi + kOffXlo;
+          const uint32_t ahi = sbase + s * kStage, alo = ahi + 16384;
+          const uint32_t bhi = ahi + 32768, blo = ahi + 49152;
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint32_t off = ks * 32;
@@ -303,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int mb = (int)(u % kp.m_blocks);
       const int i_base = mb * BM + q * 32;
 #pragma unroll 1
-      for (int g2 = 0; g2 < NGROUP / 2; ++g2) {
+      for (int g2 = 0; g2 < 2; ++g2) {
         const int cc = half + 2 * g2;   // 16-column group: r = r0 + 16 cc + 0..15
         uint32_t vr[16], vi[16];
         const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
