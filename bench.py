@@ -22,6 +22,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -81,7 +83,47 @@ def cpu_sample(n, max_steps, budget_s):
             "cores": os.cpu_count()}
 
 
-def run_cpu_sample_subprocess(n, max_steps, budget_s, timeout_s):
+def cpu_sample_batched(ninst, max_steps, budget_s):
+    """The FP64 oracle on the batched workload: instances taken in a fixed
+    order alternating 2D and 3D (setup excluded), ETD2RK steps each, until
+    ninst instances are done or the time budget is used."""
+    from oracle import schemes, tensor
+    from paper_2510_21394_gb300 import inputs
+    specs = inputs.batched_instances()
+    two = [sp for sp in specs if len(sp["ns"]) == 2]
+    three = [sp for sp in specs if len(sp["ns"]) == 3]
+    order = [x for pair in zip(two, three) for x in pair]
+    dofsteps, t_run, done, setup = 0, 0.0, 0, 0.0
+    for sp in order[:ninst]:
+        t0 = time.perf_counter()
+        P = tensor.Problem(sp["ns"], sp["boxes"], sp["alphas"], sp["nu"], sp["eta"], sp["gamma"], sp["kappa"],
+                           sp["zeta"])
+        S = tensor.Spectral(P)
+        S.F("phi", 1, TAU)
+        S.F("phi", 2, TAU)
+        setup += time.perf_counter() - t0
+        g = schemes.Nonlinearity(P)
+        u = inputs.gaussian_pulse(sp["ns"], sp["boxes"])
+        t1 = time.perf_counter()
+        u = schemes.integrate(S, g, "etd2rk", TAU, max_steps, u)
+        t_run += time.perf_counter() - t1
+        dofsteps += int(np.prod(sp["ns"])) * max_steps
+        done += 1
+        if t_run > budget_s:
+            break
+    return {"value": dofsteps / t_run, "seconds": t_run, "instances": done, "steps": max_steps, "setup_s": setup,
+            "cores": os.cpu_count()}
+
+
+def run_cpu_sample_subprocess(n, max_steps, budget_s, timeout_s, batched=False):
+    if batched:
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-batched", str(n), str(max_steps),
+               str(budget_s)]
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+        for line in r.stdout.splitlines()[::-1]:
+            if line.startswith("{"):
+                return json.loads(line)
+        raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n), str(max_steps), str(budget_s)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
     for line in r.stdout.splitlines()[::-1]:
@@ -335,6 +377,109 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def batched_config(specs, use_graph):
+    n2 = [sp["ns"][0] for sp in specs if len(sp["ns"]) == 2]
+    n3 = [sp["ns"][0] for sp in specs if len(sp["ns"]) == 3]
+    return {
+        "workload": f"batched: {len(n2)} 2D grids n^2, n ~ U[128,768], and {len(n3)} 3D grids n^3, n ~ U[48,160] "
+                    f"on (-10,10)^d; seeded alpha_mu in [1.1,1.9], nu in [0.5,2], eta, zeta in [-1,1], "
+                    f"gamma in [0,1], kappa in [0.5,2]; Gaussian pulse u0; ETD2RK, tau=1e-3",
+        "instances": len(specs), "dof_total": int(sum(int(np.prod(sp["ns"])) for sp in specs)),
+        "n2_range": [min(n2), max(n2)] if n2 else None, "n3_range": [min(n3), max(n3)] if n3 else None,
+        "scheme": "etd2rk", "tau": TAU, "precision": "bf16x3", "storage": "complex64",
+        "launch": "one CUDA graph per step (fork/join over streams)" if use_graph else "direct launches",
+        "l2": "working set of the batch (GBs) far above L2",
+        "parallelism": "replicas (one independent batch per GPU)",
+    }
+
+
+def run_batched(args, rank, world, local_rank):
+    """The batched workload: many uneven instances advanced together, one
+    CUDA-graph launch per step."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        import __graft_entry__ as g
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2510_21394_gb300 import fcgle, inputs
+    specs = inputs.batched_instances()
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    b = fcgle.Batch(specs, precision="bf16x3", stream=stream)
+    setup_s = time.perf_counter() - t0
+    u0n = [inputs.gaussian_pulse(sp["ns"], sp["boxes"]) for sp in specs]
+    u0 = [torch.from_numpy(x).to(torch.complex64).cuda() for x in u0n]
+    outs = [torch.empty_like(u) for u in u0]
+    dof = sum(int(np.prod(sp["ns"])) for sp in specs)
+    res = {}
+    for use_graph in (False, True):
+        b.integrate("etd2rk", TAU, args.warmup, u0, out=outs, use_graph=use_graph)
+        torch.cuda.synchronize()
+        clock = ClockSampler(gpu_index_for(local_rank)) if (rank == 0 and use_graph) else None
+        time.sleep(0.3 if clock else 0.0)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0, g0 = b.launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.integrate("etd2rk", TAU, args.steps, u0, out=outs, use_graph=use_graph)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        l1, g1 = b.launches()
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res[use_graph] = dict(ms=ms, launches=l1 - l0, graphs=g1 - g0, clocks=clock.stop() if clock else None)
+    for i in range(len(specs)):
+        fcgle.fcgle_sync(b.instance(i))
+    # end to end: H2D of every u0 from pinned memory, the K graph steps, D2H of every u(T)
+    hin = [torch.from_numpy(x.astype(np.complex64)).pin_memory() for x in u0n]
+    hout = [torch.empty_like(x).pin_memory() for x in hin]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    dev = [x.to("cuda", non_blocking=True) for x in hin]
+    b.integrate("etd2rk", TAU, args.steps, dev, out=outs, use_graph=True)
+    for o, h in zip(outs, hout):
+        h.copy_(o, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    nbytes = sum(x.numel() * 8 for x in hin)
+    b.close()
+    r = res[True]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            c = run_cpu_sample_subprocess(96, 5, 20.0, timeout_s=900, batched=True)
+            cpu = {"value": c["value"], "unit": UNIT, "cores": c["cores"], "kind": "oracle",
+                   "sample": f"{c['instances']} instances (alternating 2D / 3D in draw order) x {c['steps']} ETD2RK "
+                             f"steps ({c['seconds']:.1f} s), numpy FP64 tensor-form oracle, setup excluded"}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * dof * args.steps / (r["ms"] / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+                "data": "synthetic", "config": batched_config(specs, True),
+                "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
+                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+                        "note": "all u0 copied in from pinned memory and all u(T) copied out per call of K steps"},
+                # the graph run executes exactly the kernels the direct run launches
+                "gpu_launches": res[False]["launches"], "graph_launches": r["graphs"], "clocks": r["clocks"],
+                "cpu_baseline": cpu,
+                "direct_launch": {"value": world * dof * args.steps / (res[False]["ms"] / 1e3),
+                                  "ms_per_step": res[False]["ms"] / args.steps, "kernels": res[False]["launches"]},
+                "setup_s": round(setup_s, 2)}
+        print(json.dumps(line))
+    return 0
+
+
 def run_mp_only(args):
     """Raw mode products on internal-layout buffers, for kernel profiling."""
     import torch
@@ -372,12 +517,20 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", nargs=3, default=None)
+    ap.add_argument("--cpu-sample-batched", nargs=3, default=None)
     ap.add_argument("--mp-only", type=int, default=0, metavar="REPS",
                     help="only run REPS x 3 raw mode products (all directions) of the n^3 workload (profiling)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--workload", default="cube", choices=["cube", "batched"],
+                    help="cube: one 3D n^3 Krogstad instance (default); batched: 96 uneven ETD2RK instances")
     args = ap.parse_args()
     if args.mp_only:
         return run_mp_only(args)
+    if args.cpu_sample_batched:
+        k, steps, budget = int(args.cpu_sample_batched[0]), int(args.cpu_sample_batched[1]), \
+            float(args.cpu_sample_batched[2])
+        print(json.dumps(cpu_sample_batched(k, steps, budget)))
+        return 0
     if args.cpu_sample:
         n, steps, budget = int(args.cpu_sample[0]), int(args.cpu_sample[1]), float(args.cpu_sample[2])
         print(json.dumps(cpu_sample(n, steps, budget)))
@@ -393,6 +546,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        if args.workload == "batched":
+            return run_batched(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

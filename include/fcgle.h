@@ -199,6 +199,37 @@ fcgle_status fcgle_launch_count(fcgle_handle h, long long* count);
 
 fcgle_status fcgle_destroy(fcgle_handle h);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent instances (uneven sizes and parameters) advanced together.
+ * The instances are spread over nstreams internal streams (longest processing
+ * time first on the mode-product work; nstreams <= 0: min(count, 16)) and set
+ * up in parallel host threads.  fcgle_batch_integrate with use_graph != 0
+ * captures one time step of all instances (fork/join over the streams) into a
+ * CUDA graph, cached per (scheme, tau), and launches it once per step; with
+ * sources present (time-dependent steps) it enqueues the kernels directly. */
+typedef struct fcgle_batch_ctx* fcgle_batch;
+
+fcgle_status fcgle_batch_create(int count, const fcgle_params* params, void* cuda_stream, int nstreams,
+                                fcgle_batch* out);
+
+/* Handle of instance i, owned by the batch (use it for set_source /
+ * set_coefficients / apply_f / sync; do not destroy it or change its stream).
+ * Calls on it run on one of the batch's internal non-blocking streams, which
+ * are not ordered after work on the caller's stream: make their inputs ready
+ * first (e.g. synchronise the device). */
+fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h);
+
+/* nsteps steps of every instance i from u0[i] into uT[i] (device tensors in
+ * each instance's user layout and precision).  Asynchronous on the batch's
+ * stream (the stream given at creation), joined back to it at the end. */
+fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,
+                                   const void* const* u0, void* const* uT, int use_graph);
+
+/* Kernel launches issued by all instances so far and graph launches so far. */
+fcgle_status fcgle_batch_launch_count(fcgle_batch b, long long* kernels, long long* graph_launches);
+
+fcgle_status fcgle_batch_destroy(fcgle_batch b);
+
 const char* fcgle_status_string(fcgle_status s);
 
 /* Thread-local description of the last error on this thread ("" if none). */

@@ -1,10 +1,15 @@
 // C ABI entry points (include/fcgle.h): argument validation, exception to
 // status translation and the thread-local error message.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "engine.h"
 
@@ -12,6 +17,22 @@ struct fcgle_ctx {
   fcgle_params prm;
   cudaStream_t stream = nullptr;
   std::unique_ptr<fcgle::EngineBase> eng;
+};
+
+// Batch of independent instances: one stream per group of instances (longest
+// processing time first on the mode-product work), a step of all instances
+// captured once into a CUDA graph (fork / join over the streams) and replayed.
+struct fcgle_batch_ctx {
+  std::vector<fcgle_ctx*> inst;
+  cudaStream_t main = nullptr;     // the caller's stream (may be the legacy default stream)
+  cudaStream_t origin = nullptr;   // internal stream the step graph is captured from and launched on
+  cudaEvent_t enter = nullptr, leave = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> stream_of;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::map<std::pair<int, uint64_t>, cudaGraphExec_t> graphs;
+  long long graph_launches = 0;
 };
 
 namespace fcgle {
@@ -264,6 +285,193 @@ fcgle_status fcgle_destroy(fcgle_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     delete h;
   });
+}
+
+// ------------------------------------------------------------------ batches
+static void batch_free(fcgle_batch_ctx* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto* h : b->inst) delete h;
+  for (auto st : b->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->enter) cudaEventDestroy(b->enter);
+  if (b->leave) cudaEventDestroy(b->leave);
+  for (auto e : b->join) cudaEventDestroy(e);
+  delete b;
+}
+
+fcgle_status fcgle_batch_create(int count, const fcgle_params* params, void* cuda_stream, int nstreams,
+                                fcgle_batch* out) {
+  return guarded([&] {
+    if (!out) throw InvalidArg("out is NULL");
+    *out = nullptr;
+    if (count < 1 || !params) throw InvalidArg("count must be >= 1 and params non-NULL");
+    if (nstreams < 1) nstreams = std::min(count, 16);
+    nstreams = std::min(nstreams, count);
+    for (int i = 0; i < count; ++i) validate(&params[i]);
+    auto* b = new fcgle_batch_ctx;
+    try {
+      b->main = (cudaStream_t)cuda_stream;
+      b->streams.resize(nstreams);
+      b->join.resize(nstreams);
+      for (int k = 0; k < nstreams; ++k) {
+        FCGLE_CUDA(cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking));
+        FCGLE_CUDA(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+      }
+      FCGLE_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+      FCGLE_CUDA(cudaEventCreateWithFlags(&b->enter, cudaEventDisableTiming));
+      FCGLE_CUDA(cudaEventCreateWithFlags(&b->leave, cudaEventDisableTiming));
+      FCGLE_CUDA(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+      // longest processing time first: work of a step ~ N * sum_mu n_mu
+      std::vector<std::pair<double, int>> cost(count);
+      for (int i = 0; i < count; ++i) {
+        double N = 1, S = 0;
+        for (int mu = 0; mu < params[i].d; ++mu) {
+          N *= params[i].n[mu];
+          S += params[i].n[mu];
+        }
+        cost[i] = {N * S, i};
+      }
+      std::sort(cost.begin(), cost.end(), [](auto& x, auto& y) { return x.first > y.first; });
+      std::vector<double> load(nstreams, 0.0);
+      b->stream_of.assign(count, 0);
+      for (auto& c : cost) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->stream_of[c.second] = k;
+        load[k] += c.first;
+      }
+      // set the instances up in parallel host threads (the eigensolvers dominate)
+      b->inst.assign(count, nullptr);
+      std::vector<std::string> errs(count);
+      std::atomic<int> next(0);
+      const int nth = std::max(1, std::min(count, (int)std::thread::hardware_concurrency() / 2));
+      std::vector<std::thread> th;
+      for (int w = 0; w < nth; ++w)
+        th.emplace_back([&] {
+          for (int i = next++; i < count; i = next++) {
+            try {
+              auto* h = new fcgle_ctx;
+              h->prm = params[i];
+              h->stream = b->streams[b->stream_of[i]];
+              h->eng = make_engine(params[i], h->stream);
+              b->inst[i] = h;
+            } catch (const std::exception& e) {
+              errs[i] = e.what();
+            } catch (const CudaError& e) {
+              errs[i] = e.where;
+            }
+          }
+        });
+      for (auto& t : th) t.join();
+      for (int i = 0; i < count; ++i)
+        if (!b->inst[i]) throw std::runtime_error("instance " + std::to_string(i) + ": " + errs[i]);
+    } catch (...) {
+      batch_free(b);
+      throw;
+    }
+    *out = b;
+  });
+}
+
+fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h) {
+  return guarded([&] {
+    if (!b || !h) throw InvalidArg("NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) throw InvalidArg("instance index out of range");
+    *h = b->inst[i];
+  });
+}
+
+fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,
+                                   const void* const* u0, void* const* uT, int use_graph) {
+  return guarded([&] {
+    if (!b || !u0 || !uT) throw InvalidArg("NULL argument");
+    check_scheme(scheme);
+    check_tau(tau);
+    if (nsteps < 0) throw InvalidArg("nsteps must be >= 0");
+    const int n = (int)b->inst.size(), ns = (int)b->streams.size();
+    for (int i = 0; i < n; ++i)
+      if (!u0[i] || !uT[i]) throw InvalidArg("tensor pointer is NULL");
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured: all work is ordered through the internal origin stream
+    auto fork = [&] {
+      FCGLE_CUDA(cudaEventRecord(b->fork, b->origin));
+      for (auto st : b->streams) FCGLE_CUDA(cudaStreamWaitEvent(st, b->fork, 0));
+    };
+    auto join = [&] {
+      for (int k = 0; k < ns; ++k) {
+        FCGLE_CUDA(cudaEventRecord(b->join[k], b->streams[k]));
+        FCGLE_CUDA(cudaStreamWaitEvent(b->origin, b->join[k], 0));
+      }
+    };
+    FCGLE_CUDA(cudaEventRecord(b->enter, b->main));
+    FCGLE_CUDA(cudaStreamWaitEvent(b->origin, b->enter, 0));
+    fork();
+    for (int i = 0; i < n; ++i) b->inst[i]->eng->begin_steps(scheme, tau, t0, u0[i]);
+    bool replay = use_graph != 0 && nsteps > 0;
+    for (int i = 0; i < n && replay; ++i) replay = !b->inst[i]->eng->time_dependent();
+    int first = 0;
+    if (replay && scheme == FCGLE_LBDF2) {   // step 0 (linearly-implicit Euler) differs from the rest
+      for (int i = 0; i < n; ++i) b->inst[i]->eng->one_step(0);
+      first = 1;
+    }
+    if (replay && first < nsteps) {
+      join();
+      uint64_t tb;
+      std::memcpy(&tb, &tau, 8);
+      auto key = std::make_pair(scheme, tb);
+      auto it = b->graphs.find(key);
+      if (it == b->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        FCGLE_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+        try {
+          fork();
+          for (int i = 0; i < n; ++i) b->inst[i]->eng->one_step(first);
+          join();
+        } catch (...) {
+          cudaStreamEndCapture(b->origin, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        FCGLE_CUDA(cudaStreamEndCapture(b->origin, &g));
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        FCGLE_CUDA(e);
+        it = b->graphs.emplace(key, ex).first;
+      }
+      for (int k = first; k < nsteps; ++k) {
+        FCGLE_CUDA(cudaGraphLaunch(it->second, b->origin));
+        ++b->graph_launches;
+      }
+      fork();
+    } else {
+      for (int k = first; k < nsteps; ++k)
+        for (int i = 0; i < n; ++i) b->inst[i]->eng->one_step(k);
+    }
+    for (int i = 0; i < n; ++i) b->inst[i]->eng->end_steps(uT[i]);
+    join();
+    FCGLE_CUDA(cudaEventRecord(b->leave, b->origin));
+    FCGLE_CUDA(cudaStreamWaitEvent(b->main, b->leave, 0));
+  });
+}
+
+fcgle_status fcgle_batch_launch_count(fcgle_batch b, long long* kernels, long long* graph_launches) {
+  return guarded([&] {
+    if (!b) throw InvalidArg("NULL batch");
+    long long k = 0;
+    for (auto* h : b->inst) k += h->eng->launches;
+    if (kernels) *kernels = k;
+    if (graph_launches) *graph_launches = b->graph_launches;
+  });
+}
+
+fcgle_status fcgle_batch_destroy(fcgle_batch b) {
+  return guarded([&] { batch_free(b); });
 }
 
 const char* fcgle_status_string(fcgle_status s) {

@@ -232,6 +232,30 @@ class Engine : public EngineBase {
     unpack<T>(s_, B(kU), (T*)uT, st_, launches);
   }
 
+  void begin_steps(int scheme, double tau, double t0, const void* u0) override {
+    pack<T>(s_, (const T*)u0, B(kU), st_, launches);
+    prepare(scheme, tau);
+    rs_scheme_ = scheme;
+    rs_tau_ = tau;
+    rs_t0_ = t0;
+    if (scheme == FCGLE_LBDF2)
+      FCGLE_CUDA(cudaMemcpyAsync(B(kG), B(kU), 2 * s_.P * sizeof(T), cudaMemcpyDeviceToDevice, st_));
+    if (needs_uhat(scheme)) tucker(B(kU), B(kUh), true);
+  }
+  void one_step(int n) override {
+    const double t = rs_t0_ + n * rs_tau_;
+    if (rs_scheme_ == FCGLE_LBDF2) {
+      if (n == 0)
+        one_step(FCGLE_LIE, rs_tau_, t);
+      else
+        lbdf2_step(rs_tau_, t);
+    } else {
+      one_step(rs_scheme_, rs_tau_, t);
+    }
+  }
+  void end_steps(void* uT) override { unpack<T>(s_, B(kU), (T*)uT, st_, launches); }
+  bool time_dependent() const override { return gp_.nsrc > 0; }
+
   void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
     const size_t bytes = s_.N * 2 * sizeof(T);
     if (!host_stage_) host_stage_.reset(new DevBuf<T>(2 * s_.N));
@@ -611,6 +635,8 @@ class Engine : public EngineBase {
   fcgle_params prm_;
   cudaStream_t st_;
   Shape s_;
+  int rs_scheme_ = 0;
+  double rs_tau_ = 0.0, rs_t0_ = 0.0;
   Direction dir_[kMaxDim];
   std::unique_ptr<DevBuf<double>> lam_[kMaxDim];
   std::unique_ptr<DevBuf<double>> mf64_[kMaxDim][2];

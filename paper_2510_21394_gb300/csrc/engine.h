@@ -56,6 +56,15 @@ class EngineBase {
     mode_product(mu, flags & 1, X, Y);
   }
   virtual size_t internal_elems() const = 0;
+  // stepping interface (batched CUDA graphs): pack u0 and build the loop's entry
+  // state; enqueue step n; unpack the state.  No host synchronisation inside
+  // one_step, so a step can be captured into a graph.
+  virtual void begin_steps(int scheme, double tau, double t0, const void* u0) = 0;
+  virtual void one_step(int n) = 0;
+  virtual void end_steps(void* uT) = 0;
+  // true if the step depends on t through the source (a captured step then
+  // cannot be replayed for other n)
+  virtual bool time_dependent() const = 0;
   virtual size_t elem_bytes() const = 0;
   virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
   long long launches = 0;

@@ -534,9 +534,49 @@ class EngineB3 : public EngineBase {
   }
 
   // prologue (entry state of the loop), then nsteps fused steps on F32(kU)
+  // ---- time loop, split into a prologue and per-step bodies (batched graphs replay a step)
   void run(int scheme, double tau, int nsteps, double t0) {
     if (scheme < FCGLE_LIE || scheme > FCGLE_STRANG) throw InvalidArg("unknown scheme");
     if (nsteps == 0) return;
+    begin(scheme, tau, t0);
+    for (int n = 0; n < nsteps; ++n) step(n);
+  }
+
+  // entry state of the loop from u_0 in F32(kU)
+  void begin(int scheme, double tau, double t0) {
+    rs_scheme_ = scheme;
+    rs_tau_ = tau;
+    rs_t0_ = t0;
+    float* U = F32(kU);
+    SplitOut V = SP(kV), W = SP(kW);
+    const float ft = (float)tau;
+    switch (scheme) {
+      case FCGLE_LIE:
+      case FCGLE_LAWSON_EULER:
+      case FCGLE_LBDF2:
+        gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
+        break;
+      case FCGLE_STRANG:
+        flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(tau / 2), U, V);
+        FCGLE_LAUNCHED(launches);
+        break;
+      case FCGLE_LAWSON_RK2:
+        gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
+        break;
+      case FCGLE_ETD2RK:
+      case FCGLE_KROGSTAD:
+        gsplit(U, t0, 1.f, 0.f, V);                     // U^_0 = fwd(u_0)
+        tucker(V, true, b3::EpiStoreF32{P32(), F32(kUh)});
+        gsplit(U, t0, 0.f, 1.f, V);                     // G_0
+        break;
+      default: throw InvalidArg("unknown scheme");
+    }
+  }
+
+  // step n: (t_n, u_n) -> u_{n+1}; every step leaves the split input of the next one in V (and W)
+  void step(int n) {
+    const int scheme = rs_scheme_;
+    const double tau = rs_tau_, t0 = rs_t0_, t = t0 + n * tau;
     float* U = F32(kU);
     SplitOut V = SP(kV), W = SP(kW);
     const float ft = (float)tau;
@@ -544,94 +584,77 @@ class EngineB3 : public EngineBase {
       case FCGLE_LIE:
       case FCGLE_LAWSON_EULER: {
         const int kind = scheme == FCGLE_LIE ? 0 : 1;   // (1 - tau lam)^{-1} or e^{tau lam}
-        gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
-        for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleF{P32(), lf_, kind, ft, V});
-          tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t0 + (n + 1) * tau), 1.f, ft, V});
-        }
+        tucker(V, true, b3::EpiScaleF{P32(), lf_, kind, ft, V});
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 1.f, ft, V});
         break;
       }
       case FCGLE_STRANG: {
-        const b3::Flow f = flow(tau / 2);
-        flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), f, U, V);
-        FCGLE_LAUNCHED(launches);
-        for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
-          tucker(V, false, b3::EpiStrang{P32(), U, f, V});
-        }
+        tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
+        tucker(V, false, b3::EpiStrang{P32(), U, flow(tau / 2), V});
         break;
       }
       case FCGLE_LAWSON_RK2: {
         float* EA = F32(kEA);
-        gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
-        for (int n = 0; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
-          tucker(V, false, b3::EpiStoreF32{P32(), EA});
-          tucker(W, true, b3::EpiScaleF{P32(), lf_, 1, ft, W});
-          tucker(W, false, b3::EpiLawsonRK2{P32(), U, EA, gs_, gtime(t0 + (n + 1) * tau), ft, V, W});
-        }
+        tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
+        tucker(V, false, b3::EpiStoreF32{P32(), EA});
+        tucker(W, true, b3::EpiScaleF{P32(), lf_, 1, ft, W});
+        tucker(W, false, b3::EpiLawsonRK2{P32(), U, EA, gs_, gtime(t + tau), ft, V, W});
         break;
       }
       case FCGLE_LBDF2: {
-        float* Up = F32(kUp);
-        const float t23 = (float)(2.0 * tau / 3.0);
-        // first step: linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps
-        // u_0 as u_{n-1} and forms the first LBDF2 right-hand side
-        gsplit(U, t0, 1.f, ft, V);
-        tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, ft, V});
-        tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + 2 * tau), ft, V});
-        for (int n = 1; n < nsteps; ++n) {
-          tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, t23, V});
-          tucker(V, false, b3::EpiLBDF2{P32(), U, Up, gs_, gtime(t0 + (n + 2) * tau), ft, V});
-        }
+        // step 0 is linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps u_0
+        // as u_{n-1} and forms the first LBDF2 right-hand side
+        const float th = n == 0 ? ft : (float)(2.0 * tau / 3.0);
+        tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, th, V});
+        tucker(V, false, b3::EpiLBDF2{P32(), U, F32(kUp), gs_, gtime(t + 2 * tau), ft, V});
         break;
       }
       case FCGLE_ETD2RK: {
         float *Uh = F32(kUh), *Fh = F32(kFh);
-        gsplit(U, t0, 1.f, 0.f, V);                              // U^_0 = fwd(u_0)
-        tucker(V, true, b3::EpiStoreF32{P32(), Uh});
-        gsplit(U, t0, 0.f, 1.f, V);                              // G_0
-        for (int n = 0; n < nsteps; ++n) {
-          const double t = t0 + n * tau;
-          // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
-          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V});
-          // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
-          tucker(V, false, b3::EpiStageD{P32(), U, U, gs_, gtime(t + tau), gtime(t), V});
-          // S2 = tau phi_2(tau Lam) o D^;  U^ += S2
-          tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V});
-          // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
-          tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
-        }
+        // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
+        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V});
+        // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
+        tucker(V, false, b3::EpiStageD{P32(), U, U, gs_, gtime(t + tau), gtime(t), V});
+        // S2 = tau phi_2(tau Lam) o D^;  U^ += S2
+        tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V});
+        // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
       }
       case FCGLE_KROGSTAD: {
         float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *Wc = F32(kD3);
-        gsplit(U, t0, 1.f, 0.f, V);
-        tucker(V, true, b3::EpiStoreF32{P32(), Uh});
-        gsplit(U, t0, 0.f, 1.f, V);
-        for (int n = 0; n < nsteps; ++n) {
-          const double t = t0 + n * tau;
-          const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
-          // F^ = Lam o U^ + G^;  S = tau/2 phi_1(tau/2 Lam) F^
-          tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, 0.5f * ft, 0.5f * ft, 0, V});
-          // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
-          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
-          // D^_2;  S = tau (1/2 phi_1(tau/2 Lam) F^ + phi_2(tau/2 Lam) D^_2)
-          tucker(V, true, b3::EpiKrog2{P32(), lf_, Fh, D2, ft, V});
-          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
-          // D^_3;  S = tau (phi_1 F^ + 2 phi_2 D^_3);  W = part of the final combination
-          tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V});
-          tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
-          // D^_4;  S = W + tau (4 phi_3 - phi_2) D^_4;  U^ += S
-          tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V});
-          // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
-          tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, t1, 0.f, 1.f, V});
-        }
+        const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
+        // F^ = Lam o U^ + G^;  S = tau/2 phi_1(tau/2 Lam) F^
+        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, 0.5f * ft, 0.5f * ft, 0, V});
+        // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
+        tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
+        // D^_2;  S = tau (1/2 phi_1(tau/2 Lam) F^ + phi_2(tau/2 Lam) D^_2)
+        tucker(V, true, b3::EpiKrog2{P32(), lf_, Fh, D2, ft, V});
+        tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
+        // D^_3;  S = tau (phi_1 F^ + 2 phi_2 D^_3);  W = part of the final combination
+        tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V});
+        tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
+        // D^_4;  S = W + tau (4 phi_3 - phi_2) D^_4;  U^ += S
+        tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V});
+        // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, t1, 0.f, 1.f, V});
         break;
       }
       default: throw InvalidArg("unknown scheme");
     }
   }
+
+  // EngineBase stepping interface
+  void begin_steps(int scheme, double tau, double t0, const void* u0) override {
+    pack_f32((const float*)u0, F32(kU));
+    begin(scheme, tau, t0);
+  }
+  void one_step(int n) override { step(n); }
+  void end_steps(void* uT) override { unpack_f32(F32(kU), (float*)uT); }
+  bool time_dependent() const override { return gs_.nsrc > 0; }
+
+  int rs_scheme_ = 0;
+  double rs_tau_ = 0.0, rs_t0_ = 0.0;
 
   fcgle_params prm_;
   cudaStream_t st_;

@@ -39,7 +39,9 @@ PRECISIONS = {"fp64": FCGLE_FP64, "bf16x3": FCGLE_BF16X3}
 EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f", "fcgle_step",
            "fcgle_integrate", "fcgle_integrate_host", "fcgle_norm", "fcgle_sync", "fcgle_sizes",
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
-           "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients"]
+           "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
+           "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
+           "fcgle_batch_destroy"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -81,6 +83,11 @@ def _load():
         "fcgle_mode_product": [H, I, I, P, P],
         "fcgle_adjoint": [H, I, D, I, D, P, P, I, P, ctypes.POINTER(D), ctypes.POINTER(D)],
         "fcgle_set_coefficients": [H, D, D, D, D, D],
+        "fcgle_batch_create": [I, ctypes.POINTER(fcgle_params), P, I, ctypes.POINTER(H)],
+        "fcgle_batch_instance": [H, I, ctypes.POINTER(H)],
+        "fcgle_batch_integrate": [H, I, D, I, D, ctypes.POINTER(P), ctypes.POINTER(P), I],
+        "fcgle_batch_launch_count": [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+        "fcgle_batch_destroy": [H],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -122,7 +129,7 @@ def _stream(stream):
 
 
 # ------------------------------------------------------------ C ABI mirror
-def fcgle_setup(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, precision="fp64", stream=None):
+def make_params(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, precision="fp64"):
     p = fcgle_params()
     p.d = len(ns)
     for mu in range(3):
@@ -133,9 +140,46 @@ def fcgle_setup(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, prec
     p.nu, p.eta, p.gamma, p.kappa, p.zeta = map(float, (nu, eta, gamma, kappa, zeta))
     p.fd_order = int(fd_order)
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return p
+
+
+def fcgle_setup(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order=2, precision="fp64", stream=None):
+    p = make_params(ns, boxes, alphas, nu, eta, gamma, kappa, zeta, fd_order, precision)
     h = ctypes.c_void_p()
     _check(_lib.fcgle_setup(ctypes.byref(p), _stream(stream), ctypes.byref(h)))
     return h
+
+
+def fcgle_batch_create(params_list, stream=None, nstreams=0):
+    arr = (fcgle_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(_lib.fcgle_batch_create(len(params_list), arr, _stream(stream), int(nstreams), ctypes.byref(b)))
+    return b
+
+
+def fcgle_batch_instance(b, i):
+    h = ctypes.c_void_p()
+    _check(_lib.fcgle_batch_instance(b, int(i), ctypes.byref(h)))
+    return h
+
+
+def fcgle_batch_integrate(b, scheme, tau, nsteps, t0, u0_list, uT_list, use_graph=True):
+    scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    n = len(u0_list)
+    a = (ctypes.c_void_p * n)(*[_ptr(t).value for t in u0_list])
+    o = (ctypes.c_void_p * n)(*[_ptr(t).value for t in uT_list])
+    _check(_lib.fcgle_batch_integrate(b, scheme, float(tau), int(nsteps), float(t0), a, o, int(bool(use_graph))))
+
+
+def fcgle_batch_launch_count(b):
+    k = ctypes.c_longlong()
+    g = ctypes.c_longlong()
+    _check(_lib.fcgle_batch_launch_count(b, ctypes.byref(k), ctypes.byref(g)))
+    return k.value, g.value
+
+
+def fcgle_batch_destroy(b):
+    _check(_lib.fcgle_batch_destroy(b))
 
 
 def fcgle_set_stream(h, stream=None):
@@ -305,3 +349,40 @@ class Solver:
 
     def launches(self):
         return fcgle_launch_count(self.h)
+
+
+class Batch:
+    """Many independent instances advanced together (see fcgle_batch_* in include/fcgle.h).
+
+    specs: list of dicts with keys ns, boxes, alphas, nu, eta, gamma, kappa, zeta
+    (and optionally fd_order); all instances share one precision."""
+
+    def __init__(self, specs, precision="bf16x3", stream=None, nstreams=0):
+        self.precision = precision
+        self.dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.shapes = [tuple(reversed(list(sp["ns"]))) for sp in specs]
+        plist = [make_params(sp["ns"], sp["boxes"], sp["alphas"], sp["nu"], sp["eta"], sp["gamma"], sp["kappa"],
+                             sp["zeta"], sp.get("fd_order", 2), precision) for sp in specs]
+        self.b = fcgle_batch_create(plist, stream, nstreams)
+
+    def instance(self, i):
+        return fcgle_batch_instance(self.b, i)
+
+    def integrate(self, scheme, tau, nsteps, u0_list, t0=0.0, out=None, use_graph=True):
+        out = [torch.empty_like(u) for u in u0_list] if out is None else out
+        fcgle_batch_integrate(self.b, scheme, tau, nsteps, t0, u0_list, out, use_graph)
+        return out
+
+    def launches(self):
+        return fcgle_batch_launch_count(self.b)
+
+    def close(self):
+        if self.b is not None:
+            fcgle_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,6 +18,9 @@ Workloads (recipes; sizes as in the paper's 2D/3D experiments):
   padded FFT convolution), then standardised.
 * ``polynomial_manufactured``: the paper's Example 1,
   u = e^{-i t} prod_mu (1 - x_mu^2)^4 on (-1,1)^d, with its continuous source.
+* ``batched_instances``: many independent problems of uneven sizes with
+  seeded parameters (square 2D and cubic 3D grids on (-10,10)^d), each started
+  from ``gaussian_pulse``.
 """
 import math
 
@@ -201,3 +204,26 @@ def gaussian_random_phase(ns, boxes, seed=1, corr=1.0):
 def gaussian_pulse(ns, boxes):
     X = mesh(ns, boxes)
     return np.broadcast_to(np.exp(-sum(Xm ** 2 for Xm in X)), _shape(ns)).astype(np.complex128)
+
+
+def batched_instances(n2=64, n3=32, range2=(128, 768), range3=(48, 160), seed=2):
+    """Seeded list of problem specs (dicts: ns, boxes, alphas, nu, eta, gamma,
+    kappa, zeta): n2 square 2D grids with n drawn uniformly from range2, then
+    n3 cubic 3D grids from range3, on (-10,10)^d.  Per instance the draws are
+    taken in this order from one PCG64 stream: n, alpha_mu in [1.1, 1.9]
+    (one per direction), nu in [0.5, 2], eta in [-1, 1], zeta in [-1, 1],
+    gamma in [0, 1], kappa in [0.5, 2]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for d, cnt, (lo, hi) in ((2, n2, range2), (3, n3, range3)):
+        for _ in range(cnt):
+            n = int(rng.integers(lo, hi + 1))
+            alphas = [float(a) for a in rng.uniform(1.1, 1.9, d)]
+            nu = float(rng.uniform(0.5, 2.0))
+            eta = float(rng.uniform(-1.0, 1.0))
+            zeta = float(rng.uniform(-1.0, 1.0))
+            gamma = float(rng.uniform(0.0, 1.0))
+            kappa = float(rng.uniform(0.5, 2.0))
+            out.append(dict(ns=[n] * d, boxes=[(-10.0, 10.0)] * d, alphas=alphas, nu=nu, eta=eta, gamma=gamma,
+                            kappa=kappa, zeta=zeta))
+    return out

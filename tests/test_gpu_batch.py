@@ -1,0 +1,92 @@
+"""Batched instances: each instance of a batch (CUDA-graph replay or direct
+enqueue over several streams) equals the same instance run alone, bit for bit,
+and one instance matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import schemes, tensor
+from paper_2510_21394_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _specs(seed=2, n2=4, n3=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for d, cnt, lo, hi in ((2, n2, 20, 90), (3, n3, 8, 30)):
+        for _ in range(cnt):
+            n = int(rng.integers(lo, hi + 1))
+            out.append(dict(ns=[n] * d, boxes=[(-10.0, 10.0)] * d, alphas=list(rng.uniform(1.1, 1.9, d)),
+                            nu=float(rng.uniform(0.5, 2)), eta=float(rng.uniform(-1, 1)),
+                            gamma=float(rng.uniform(0, 1)), kappa=float(rng.uniform(0.5, 2)),
+                            zeta=float(rng.uniform(-1, 1))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_21394_gb300 import fcgle
+    return fcgle
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+@pytest.mark.parametrize("scheme", ["etd2rk", "lbdf2", "krogstad"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_single_runs(fc, prec, scheme, graph):
+    specs = _specs()
+    dt = torch.complex64 if prec == "bf16x3" else torch.complex128
+    b = fc.Batch(specs, precision=prec, nstreams=3)
+    u0 = [torch.from_numpy(inputs.gaussian_pulse(sp["ns"], [(-3.0, 3.0)] * len(sp["ns"]))).to(dt).cuda()
+          for sp in specs]
+    tau, m = 5e-3, 6
+    outs = b.integrate(scheme, tau, m, u0, use_graph=graph)
+    outs2 = b.integrate(scheme, tau, m, u0, use_graph=graph)   # cached graph, same result
+    torch.cuda.synchronize()
+    k, gl = b.launches()
+    assert k > 0 and (gl > 0) == (graph)
+    for sp, u, o, o2 in zip(specs, u0, outs, outs2):
+        s = fc.Solver(sp["ns"], sp["boxes"], sp["alphas"], sp["nu"], sp["eta"], sp["gamma"], sp["kappa"],
+                      sp["zeta"], precision=prec)
+        ref = s.integrate(scheme, tau, m, u)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref) and torch.equal(o2, ref)
+        s.close()
+    b.close()
+
+
+def test_batch_instance_against_oracle(fc):
+    specs = _specs(seed=5, n2=2, n3=2)
+    b = fc.Batch(specs, precision="bf16x3")
+    u0n = [inputs.gaussian_pulse(sp["ns"], [(-3.0, 3.0)] * len(sp["ns"])) for sp in specs]
+    u0 = [torch.from_numpy(x).to(torch.complex64).cuda() for x in u0n]
+    outs = b.integrate("etd2rk", 5e-3, 8, u0)
+    torch.cuda.synchronize()
+    for sp, x0, o in zip(specs, u0n, outs):
+        P = tensor.Problem(sp["ns"], sp["boxes"], sp["alphas"], sp["nu"], sp["eta"], sp["gamma"], sp["kappa"],
+                           sp["zeta"])
+        ref = schemes.integrate(tensor.Spectral(P), schemes.Nonlinearity(P), "etd2rk", 5e-3, 8,
+                                x0.astype(np.complex64).astype(np.complex128))
+        got = o.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    b.close()
+
+
+def test_batch_with_source_falls_back_to_direct_launches(fc):
+    specs = _specs(seed=7, n2=2, n3=1)
+    b = fc.Batch(specs, precision="bf16x3")
+    sp = specs[0]
+    h = b.instance(0)
+    S = torch.ones(tuple(reversed(sp["ns"])), dtype=torch.complex64, device="cuda")
+    torch.cuda.synchronize()               # set_source runs on the instance's internal stream
+    fc.fcgle_set_source(h, [-1.0], [S])
+    u0 = [torch.zeros(tuple(reversed(x["ns"])), dtype=torch.complex64, device="cuda") for x in specs]
+    outs = b.integrate("etd2rk", 1e-2, 3, u0, use_graph=True)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        fc.fcgle_sync(b.instance(i))       # no bounded device wait gave up
+    assert b.launches()[1] == 0            # no graph: the source makes the steps time dependent
+    assert float(torch.abs(outs[0]).max()) > 0 and float(torch.abs(outs[1]).max()) == 0
+    b.close()

@@ -65,3 +65,19 @@ def test_seeded_inputs_are_deterministic():
     np.testing.assert_allclose(np.abs(a), np.abs(inputs.gaussian_pulse([12, 10, 8], [(-10, 10)] * 3)), rtol=1e-14)
     c = inputs.sech_pulse_noise([6, 5], [(-20, 20)] * 2, seed=0)
     assert c.shape == (5, 6) and c.dtype == np.complex128
+
+
+def test_batched_instances_ranges_and_determinism():
+    a = inputs.batched_instances()
+    b = inputs.batched_instances()
+    assert a == b and len(a) == 96
+    two = [s for s in a if len(s["ns"]) == 2]
+    three = [s for s in a if len(s["ns"]) == 3]
+    assert len(two) == 64 and len(three) == 32
+    assert all(128 <= s["ns"][0] <= 768 and s["ns"][0] == s["ns"][1] for s in two)
+    assert all(48 <= s["ns"][0] <= 160 and len(set(s["ns"])) == 1 for s in three)
+    for s in a:
+        assert all(1.1 <= al <= 1.9 for al in s["alphas"]) and len(s["alphas"]) == len(s["ns"])
+        assert 0.5 <= s["nu"] <= 2 and -1 <= s["eta"] <= 1 and -1 <= s["zeta"] <= 1
+        assert 0 <= s["gamma"] <= 1 and 0.5 <= s["kappa"] <= 2
+        assert s["boxes"] == [(-10.0, 10.0)] * len(s["ns"])
