@@ -166,6 +166,41 @@ fcgle_status fcgle_adjoint(fcgle_handle h, int scheme, double tau, int nsteps, d
  * tensor, written to *out_host (synchronises the stream). */
 fcgle_status fcgle_norm(fcgle_handle h, const void* u, double* out_host);
 
+/* The same discrete L2 norm without a handle and without allocating device
+ * memory.  The paper has no counterpart: this is a library convenience.
+ *
+ * Who needs it: fcgle_norm needs a handle, and fcgle_setup allocates about
+ * fifteen state-sized work tensors; a caller that only wants the norm of a
+ * tensor it already holds cannot always afford that, e.g. a monitor running
+ * beside a solve that has already committed the device memory to its own
+ * tensors, or code that must not call cudaMalloc/cudaFree (which synchronise
+ * the device) while other work is in flight.
+ *
+ * p:   only d, n[], a[], b[] and precision are read (the cell volume is
+ *      prod_mu (b_mu - a_mu) / (n_mu + 1), as in fcgle_norm); the other fields
+ *      are ignored.
+ * u:   device tensor in the user layout, complex128 (FCGLE_FP64) or complex64
+ *      (FCGLE_BF16X3), caller-owned; read in place.
+ * cuda_stream: the stream the two reduction kernels run on (NULL: the legacy
+ *      default stream); the call synchronises it before returning.
+ * out_host: the norm, sqrt(cell * sum_j |u_j|^2), accumulated in FP64.
+ *
+ * Scratch: a fixed array of 32769 doubles (256 KB) in the library's static
+ * device memory holds one partial sum per chunk of 8192 entries, so at most
+ * 268435456 (2^28) complex entries are accepted; larger tensors are rejected
+ * with FCGLE_ERR_INVALID_ARG before anything runs on the device.  Every scratch
+ * slot is written before it is read: nothing has to start at zero.  The fixed
+ * chunking makes the result bitwise reproducible.
+ *
+ * Setup: the first call on each device (with that device current) looks up the
+ * scratch array's device address once; make that first call before any stream
+ * capture begins.  Nothing is promised about capturing calls into a graph.
+ *
+ * Concurrency: there is one scratch array per device and process, so calls
+ * that overlapped on one device would race on it; the library serialises them
+ * with a host lock held until the call returns. */
+fcgle_status fcgle_norm_static(const fcgle_params* p, const void* u, void* cuda_stream, double* out_host);
+
 /* Synchronises the handle's stream and reports device-side failures of the
  * work enqueued so far: FCGLE_ERR_TIMEOUT if a bounded wait inside a
  * tensor-core kernel gave up (its output is then invalid), FCGLE_ERR_CUDA on

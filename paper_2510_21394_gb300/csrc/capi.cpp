@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "norm_static.h"
 
 struct fcgle_ctx {
   fcgle_params prm;
@@ -233,6 +234,24 @@ fcgle_status fcgle_norm(fcgle_handle h, const void* u, double* out_host) {
     check_handle(h);
     if (!u || !out_host) throw InvalidArg("pointer is NULL");
     *out_host = h->eng->norm(u);
+  });
+}
+
+fcgle_status fcgle_norm_static(const fcgle_params* p, const void* u, void* cuda_stream, double* out_host) {
+  return guarded([&] {
+    if (!p || !u || !out_host) throw InvalidArg("pointer is NULL");
+    if (p->d < 1 || p->d > 3) throw InvalidArg("d must be 1, 2 or 3");
+    unsigned long long N = 1;
+    double cell = 1.0;
+    for (int mu = 0; mu < p->d; ++mu) {
+      if (p->n[mu] < 1) throw InvalidArg("n_mu must be >= 1");
+      if (!(p->b[mu] > p->a[mu])) throw InvalidArg("b_mu must exceed a_mu");
+      N *= (unsigned long long)p->n[mu];
+      cell *= (p->b[mu] - p->a[mu]) / (p->n[mu] + 1.0);
+    }
+    if (p->precision != FCGLE_FP64 && p->precision != FCGLE_BF16X3) throw InvalidArg("unknown precision");
+    const double s = norm_static_sumsq(u, p->precision == FCGLE_FP64, N, (cudaStream_t)cuda_stream);
+    *out_host = std::sqrt(cell * s);
   });
 }
 

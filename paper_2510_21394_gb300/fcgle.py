@@ -41,7 +41,7 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
-           "fcgle_batch_destroy"]
+           "fcgle_batch_destroy", "fcgle_norm_static"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -88,6 +88,7 @@ def _load():
         "fcgle_batch_integrate": [H, I, D, I, D, ctypes.POINTER(P), ctypes.POINTER(P), I],
         "fcgle_batch_launch_count": [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         "fcgle_batch_destroy": [H],
+        "fcgle_norm_static": [ctypes.POINTER(fcgle_params), P, P, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -233,6 +234,16 @@ def fcgle_adjoint(h, scheme, tau, nsteps, t0, u0, u_target, ckpt_every, grad_u0)
 def fcgle_norm(h, u):
     out = ctypes.c_double()
     _check(_lib.fcgle_norm(h, _ptr(u), ctypes.byref(out)))
+    return out.value
+
+
+def fcgle_norm_static(params, u, stream=None):
+    """Discrete L2 norm without a handle or device allocation; u is a device
+    tensor or a raw device address (int)."""
+    out = ctypes.c_double()
+    ptr = ctypes.c_void_p(u) if isinstance(u, int) else _ptr(u)
+    st = ctypes.c_void_p(0) if (stream is None and isinstance(u, int)) else _stream(stream)
+    _check(_lib.fcgle_norm_static(ctypes.byref(params), ptr, st, ctypes.byref(out)))
     return out.value
 
 
