@@ -193,7 +193,7 @@ def ncu_traffic(n):
     """DRAM bytes per launch of the mode-product kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     src = os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", "b3_kernel.cuh")
-    prof = os.path.join(ROOT, "profiles", "mp_bf16x3_256cube.md")
+    prof = os.path.join(ROOT, "profiles", "mp_b3_plain_256cube.md")
     if not os.path.exists(prof):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -212,6 +212,25 @@ def gpu_index_for(local_rank):
         if local_rank < len(ids):
             return ids[local_rank]
     return str(local_rank)
+
+
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(x, world):
+    """Largest value of x over all ranks (x itself at world size 1); works on
+    NCCL (CUDA tensor) and gloo (CPU tensor) process groups."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, steps, seconds, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
 
 
 # -------------------------------------------------------------- main arms
@@ -280,13 +299,10 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     launches = solver.launches() - l0
     solver.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     clocks = clock.stop() if clock else None
     dof = n ** 3
-    value = world * dof * args.steps / (ms / 1e3)
+    value = aggregate_rate(dof, args.steps, ms / 1e3, world)
 
     # ---- dominant kernel: the split-BF16 mode product, timed alone on the same stream
     P = fcgle.fcgle_internal_elems(solver.h)
@@ -322,8 +338,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     solver.integrate_host("krogstad", TAU, args.steps, hin, hout)
-    e2e_s = time.perf_counter() - t1
-    e2e = {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t1, world)
+    e2e = {"value": aggregate_rate(dof, args.steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": hin.numel() * 8 / args.steps, "d2h_bytes_per_step": hout.numel() * 8 / args.steps,
            "note": "fcgle_integrate_host: one H2D of u0 (pinned) and one D2H of u(T) per call of K steps, "
                    "synchronised, wall clock"}
@@ -432,10 +448,7 @@ def run_batched(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         l1, g1 = b.launches()
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         res[use_graph] = dict(ms=ms, launches=l1 - l0, graphs=g1 - g0, clocks=clock.stop() if clock else None)
     for i in range(len(specs)):
         fcgle.fcgle_sync(b.instance(i))
@@ -449,7 +462,7 @@ def run_batched(args, rank, world, local_rank):
     for o, h in zip(outs, hout):
         h.copy_(o, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t1
+    e2e_s = max_over_ranks(time.perf_counter() - t1, world)
     nbytes = sum(x.numel() * 8 for x in hin)
     b.close()
     r = res[True]
@@ -463,17 +476,17 @@ def run_batched(args, rank, world, local_rank):
         except Exception as e:
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     if rank == 0:
-        line = {"metric": METRIC, "value": world * dof * args.steps / (r["ms"] / 1e3), "unit": UNIT,
+        line = {"metric": METRIC, "value": aggregate_rate(dof, args.steps, r["ms"] / 1e3, world), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
                 "data": "synthetic", "config": batched_config(specs, True),
-                "e2e": {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
+                "e2e": {"value": aggregate_rate(dof, args.steps, e2e_s, world), "unit": UNIT,
                         "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                         "note": "all u0 copied in from pinned memory and all u(T) copied out per call of K steps"},
                 # the graph run executes exactly the kernels the direct run launches
                 "gpu_launches": res[False]["launches"], "graph_launches": r["graphs"], "clocks": r["clocks"],
                 "cpu_baseline": cpu,
-                "direct_launch": {"value": world * dof * args.steps / (res[False]["ms"] / 1e3),
+                "direct_launch": {"value": aggregate_rate(dof, args.steps, res[False]["ms"] / 1e3, world),
                                   "ms_per_step": res[False]["ms"] / args.steps, "kernels": res[False]["launches"]},
                 "setup_s": round(setup_s, 2)}
         print(json.dumps(line))
