@@ -16,16 +16,16 @@
 // r0..r0+63 of the real plane (columns 0..63) and of the imaginary plane
 // (columns 64..127), so each epilogue thread sees complete complex values.
 //
-// Warp roles (10 warps, one CTA per SM, persistent over (r-tile, i-block)):
+// Warp roles (one CTA per SM, persistent over (r-tile, i-block)):
 //   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x 64 x 64)
 //               bf16 chunks, SWIZZLE_128B, straight into the MMA layout.
 //   warp 1      TMEM allocator and single-thread MMA issuer (3 MMAs per k-step).
-//   warps 2-9   epilogue: TMEM -> registers, then either split + TMA bulk
-//               tensor stores of 32 x 16 boxes (plain mode products), or an
-//               smem transpose and a functor on coalesced (i, r) runs.  Warp w
-//               reads TMEM lane quarter w % 4 and column groups (w - 2) / 4 and
-//               (w - 2) / 4 + 2.
-// Pipelines: 3 smem stages (64 KB each), 2 TMEM accumulators (2 x 128 columns).
+//   warps 2..  epilogue (8 or 16 warps, see Cfg): TMEM -> registers, then
+//               either split + TMA bulk tensor stores of 32 x 16 boxes (plain
+//               mode products), or an smem transpose and a functor on
+//               coalesced (i, r) runs.  Warp w reads TMEM lane quarter w % 4.
+// Pipelines: 3 or 2 smem stages (64 KB each), 2 TMEM accumulators (2 x 128
+// columns).
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error code in *err, drains its own TMA and MMA work, frees its
 // TMEM and returns.
@@ -43,16 +43,29 @@ constexpr int BM = 128;     // output indices i per MMA
 constexpr int BR = 64;      // r indices per tile (x 2 planes = MMA N)
 constexpr int BN = 2 * BR;  // MMA N
 constexpr int BK = 64;      // k per chunk (one 128-byte bf16 row)
-constexpr int NSTAGE = 3;
-constexpr int NEPI = 8;     // epilogue warps
-constexpr int NTHREADS = 32 * (2 + NEPI);
 
 constexpr uint32_t kStage = 65536;   // M_hi 16K | M_lo 16K | X_hi 16K | X_lo 16K
-constexpr uint32_t kOffEpi = NSTAGE * kStage;
 constexpr uint32_t kEpiWarp = 32 * 33 * 4;
-constexpr uint32_t kOffBar = kOffEpi + NEPI * kEpiWarp;
-constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;   // + barriers + alignment slack
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+// Launch shape per epilogue kind.  The plain product (TMA-store epilogue) is
+// bound by the operand stream: 8 epilogue warps and 3 smem stages.  Fused
+// epilogues read and write several more tensors per element, so their time
+// goes into the epilogue's global loads: 16 epilogue warps (twice the loads in
+// flight) and 2 stages, which is all the shared memory then leaves.
+// Each accumulator tile is 4 TMEM lane quarters x 4 groups of 16 r columns;
+// an epilogue warp owns quarter warp % 4 and 16 / nepi of the groups.
+template <class Epi>
+struct Cfg {
+  static constexpr int kEpi = Epi::kTmaStore ? 8 : 16;
+  static constexpr int kStages = Epi::kTmaStore ? 3 : 2;
+  static constexpr int kThreads = 32 * (2 + kEpi);
+  static constexpr int kGroups = 16 / kEpi;   // 16-column groups per epilogue warp
+  static constexpr uint32_t kOffEpi = kStages * kStage;
+  static constexpr uint32_t kOffBar = kOffEpi + kEpi * kEpiWarp;
+  static constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;   // + barriers + alignment slack
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
+  static_assert(kEpi % 4 == 0 && 16 % kEpi == 0, "epilogue warps cover 4 quarters x 4 groups");
+};
 
 constexpr unsigned long long kTimeoutNs = 2000000000ull;   // 2 s per wait
 
@@ -172,11 +185,15 @@ __device__ __forceinline__ uint32_t split_pair(float a, float b, uint32_t& lo) {
 // store(q, i, r, re, im, in) for each, so that the operand loads of a batch
 // are in flight together.
 template <class Epi>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                  const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                  const KParams kp, const Epi epi) {
+  constexpr int NSTAGE = Cfg<Epi>::kStages;
+  constexpr int NEPI = Cfg<Epi>::kEpi;
+  constexpr uint32_t kOffEpi = Cfg<Epi>::kOffEpi;
+  constexpr uint32_t kOffBar = Cfg<Epi>::kOffBar;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -285,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;  // which two of the four 16-column groups
+    const int half = (warp - 2) >> 2;  // first of this warp's 16-column groups
     float* stg = reinterpret_cast<float*>(smem + kOffEpi + (warp - 2) * kEpiWarp);
     const int rr = lane & 15, hrow = (lane >> 4) * 16;
     uint32_t t = 0;
@@ -297,8 +314,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int mb = (int)(u % kp.m_blocks);
       const int i_base = mb * BM + q * 32;
 #pragma unroll 1
-      for (int g2 = 0; g2 < 2; ++g2) {
-        const int cc = half + 2 * g2;   // 16-column group: r = r0 + 16 cc + 0..15
+      for (int g2 = 0; g2 < Cfg<Epi>::kGroups; ++g2) {
+        const int cc = half + (NEPI / 4) * g2;   // 16-column group: r = r0 + 16 cc + 0..15
         uint32_t vr[16], vi[16];
         const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
         tmem_ld16(tl, vr);

@@ -415,7 +415,7 @@ class EngineB3 : public EngineBase {
   template <class Epi>
   static void set_smem_attr() {
     FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)b3::kSmemBytes));
+                                    (int)b3::Cfg<Epi>::kSmemBytes));
   }
 
   void prepare_matrix(const double* M, int p, Mat& m) {
@@ -472,7 +472,8 @@ class EngineB3 : public EngineBase {
       encode_bf16_out(&tyh, tma_out->hi, (uint64_t)R, (uint64_t)s_.p[mu]);
       encode_bf16_out(&tyl, tma_out->lo, (uint64_t)R, (uint64_t)s_.p[mu]);
     }
-    b3::mp_b3_kernel<Epi><<<grid, b3::NTHREADS, b3::kSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, epi);
+    b3::mp_b3_kernel<Epi><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_>>>(
+        txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, epi);
     FCGLE_LAUNCHED(launches);
   }
 
