@@ -313,28 +313,41 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
       const long long tile = u / kp.m_blocks;
       const int mb = (int)(u % kp.m_blocks);
       const int i_base = mb * BM + q * 32;
-#pragma unroll 1
-      for (int g2 = 0; g2 < Cfg<Epi>::kGroups; ++g2) {
-        const int cc = half + (NEPI / 4) * g2;   // 16-column group: r = r0 + 16 cc + 0..15
-        uint32_t vr[16], vi[16];
+      // all of this warp's accumulator columns into registers, then hand the
+      // accumulator back to the MMA warp before any store or functor work
+      constexpr int NG = Cfg<Epi>::kGroups;
+      uint32_t vr[NG][16], vi[NG][16];
+#pragma unroll
+      for (int g2 = 0; g2 < NG; ++g2) {
+        const int cc = half + (NEPI / 4) * g2;
         const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
-        tmem_ld16(tl, vr);
-        tmem_ld16(tl + BR, vi);
-        tmem_wait_ld();
+        tmem_ld16(tl, vr[g2]);
+        tmem_ld16(tl + BR, vi[g2]);
+      }
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(a));
+#pragma unroll
+      for (int g2 = 0; g2 < NG; ++g2) {
+        const int cc = half + (NEPI / 4) * g2;   // 16-column group: r = r0 + 16 cc + 0..15
         if constexpr (Epi::kTmaStore) {
-          // four 32 x 16 bf16 boxes (re hi, re lo, im hi, im lo); row = this lane's i
+          // four 32 x 16 bf16 boxes (re hi, re lo, im hi, im lo); row = this lane's i.
+          // The previous group's stores must have finished reading the box.
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
           uint32_t* box = reinterpret_cast<uint32_t*>(stg);
 #pragma unroll
           for (int j = 0; j < 16; j += 8) {
             uint4 rh, rl, ih, il;
-            rh.x = split_pair(__uint_as_float(vr[j + 0]), __uint_as_float(vr[j + 1]), rl.x);
-            rh.y = split_pair(__uint_as_float(vr[j + 2]), __uint_as_float(vr[j + 3]), rl.y);
-            rh.z = split_pair(__uint_as_float(vr[j + 4]), __uint_as_float(vr[j + 5]), rl.z);
-            rh.w = split_pair(__uint_as_float(vr[j + 6]), __uint_as_float(vr[j + 7]), rl.w);
-            ih.x = split_pair(__uint_as_float(vi[j + 0]), __uint_as_float(vi[j + 1]), il.x);
-            ih.y = split_pair(__uint_as_float(vi[j + 2]), __uint_as_float(vi[j + 3]), il.y);
-            ih.z = split_pair(__uint_as_float(vi[j + 4]), __uint_as_float(vi[j + 5]), il.z);
-            ih.w = split_pair(__uint_as_float(vi[j + 6]), __uint_as_float(vi[j + 7]), il.w);
+            rh.x = split_pair(__uint_as_float(vr[g2][j + 0]), __uint_as_float(vr[g2][j + 1]), rl.x);
+            rh.y = split_pair(__uint_as_float(vr[g2][j + 2]), __uint_as_float(vr[g2][j + 3]), rl.y);
+            rh.z = split_pair(__uint_as_float(vr[g2][j + 4]), __uint_as_float(vr[g2][j + 5]), rl.z);
+            rh.w = split_pair(__uint_as_float(vr[g2][j + 6]), __uint_as_float(vr[g2][j + 7]), rl.w);
+            ih.x = split_pair(__uint_as_float(vi[g2][j + 0]), __uint_as_float(vi[g2][j + 1]), il.x);
+            ih.y = split_pair(__uint_as_float(vi[g2][j + 2]), __uint_as_float(vi[g2][j + 3]), il.y);
+            ih.z = split_pair(__uint_as_float(vi[g2][j + 4]), __uint_as_float(vi[g2][j + 5]), il.z);
+            ih.w = split_pair(__uint_as_float(vi[g2][j + 6]), __uint_as_float(vi[g2][j + 7]), il.w);
             const int w = lane * 8 + j / 2;   // 32-bit word of this row's 16 bf16
             *reinterpret_cast<uint4*>(box + 0 * 256 + w) = rh;
             *reinterpret_cast<uint4*>(box + 1 * 256 + w) = rl;
@@ -351,14 +364,13 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
             tma_store_3d(&tm_yhi, sb + 2 * 1024, x, i_base, 1);
             tma_store_3d(&tm_ylo, sb + 3 * 1024, x, i_base, 1);
             bulk_commit();
-            bulk_wait_read0();   // staging reusable once the stores have read it
           }
           __syncwarp();
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            stg[lane * 33 + j] = __uint_as_float(vr[j]);
-            stg[lane * 33 + 16 + j] = __uint_as_float(vi[j]);
+            stg[lane * 33 + j] = __uint_as_float(vr[g2][j]);
+            stg[lane * 33 + 16 + j] = __uint_as_float(vi[g2][j]);
           }
           __syncwarp();
           constexpr int B = Epi::kBatch;
@@ -415,9 +427,6 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
           __syncwarp();
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty(a));
     }
   }
 
