@@ -189,14 +189,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    """sha256[:16] of the plain mode-product kernel's sources (b3_plain.cuh, then b3_kernel.cuh)."""
+    h = hashlib.sha256()
+    for f in ("b3_plain.cuh", "b3_kernel.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(n):
     """DRAM bytes per launch of the mode-product kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    src = os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", "b3_kernel.cuh")
     prof = os.path.join(ROOT, "profiles", "mp_b3_plain_256cube.md")
     if not os.path.exists(prof):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     text = open(prof).read()
     m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic bytes per launch \(scaled to %d\^3\):\s*([0-9.eE+]+)" % n, text)
@@ -328,7 +335,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = mp_bytes / (mp_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": ncu_traffic(n),
-                "kernel": "mp_b3_kernel<EpiStoreSplit> (one 256^3 mode product, split in/out)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                "kernel": "mp_b3_plain_kernel (one 256^3 mode product, split in/out)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
                 "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
     del X, Y
 

@@ -9,10 +9,9 @@
 //   * the stage combinations of Eq. krogstad-m and the other schemes,
 // writing FP32 planar tensors and/or split (hi, lo) bf16 tensors that feed
 // the next mode product.  Each functor is a plain struct passed by value with
-//   kTmaStore  true: no functor call, the kernel stores the product split
-//              through TMA bulk tensor stores (needs R % 8 == 0);
 //   kIn, kBatch, load<V>(q, i, r, in), store<V>(q, i, r, re, im, in): the
 //              kernel loads the operands of kBatch groups first, then stores.
+// (The plain split product without a pointwise stage is b3_plain.cuh.)
 // V = 4 when R % 4 == 0 (16-byte FP32 and 8-byte split accesses, q % 4 == 0),
 // V = 1 otherwise.  Plane indices are 32-bit (the host requires 2 P < 2^32).
 #pragma once
@@ -258,20 +257,8 @@ __device__ __forceinline__ void fspec(int kind, float zr, float zi, float& fr, f
 
 // ---------------------------------------------------------------- functors
 #define FCGLE_EPI(IN, BATCH)              \
-  static constexpr bool kTmaStore = false; \
   static constexpr int kIn = IN;           \
   static constexpr int kBatch = BATCH;
-
-// product -> split, through TMA stores
-struct EpiStoreSplit {
-  static constexpr bool kTmaStore = true;
-  static constexpr int kIn = 0;
-  static constexpr int kBatch = 1;
-  template <int V>
-  __device__ void load(uint32_t, int, uint32_t, float (&)[1][V]) const {}
-  template <int V>
-  __device__ void store(uint32_t, int, uint32_t, const float (&)[V], const float (&)[V], const float (&)[1][V]) const {}
-};
 
 // product -> split, element stores (any R)
 struct EpiStoreSplitGen {

@@ -1,5 +1,6 @@
 // Split-BF16 mu-mode product on the sm_103a tensor cores (tcgen05 + TMEM + TMA)
-// with a fused pointwise epilogue.
+// with a fused pointwise epilogue (the last mode product of a Tucker operator
+// that carries a scheme's pointwise stage).
 //
 // One launch computes, in the rotating layout of common.h,
 //     acc[c][i][r] = sum_k M[i][k] X[c][r][k]              (Sec. 3.2, one mode product)
@@ -20,12 +21,10 @@
 //   warp 0      TMA producer: M_hi, M_lo (128 x 64) and X_hi, X_lo (2 x 64 x 64)
 //               bf16 chunks, SWIZZLE_128B, straight into the MMA layout.
 //   warp 1      TMEM allocator and single-thread MMA issuer (3 MMAs per k-step).
-//   warps 2..  epilogue (8 or 16 warps, see Cfg): TMEM -> registers, then
-//               either split + TMA bulk tensor stores of 32 x 16 boxes (plain
-//               mode products), or an smem transpose and a functor on
-//               coalesced (i, r) runs.  Warp w reads TMEM lane quarter w % 4.
-// Pipelines: 3 or 2 smem stages (64 KB each), 2 TMEM accumulators (2 x 128
-// columns).
+//   warps 2-17  epilogue (see Cfg): TMEM -> registers, an smem transpose and
+//               the functor on coalesced (i, r) runs.  Warp w reads TMEM lane
+//               quarter w % 4.
+// Pipelines: 2 smem stages (64 KB each), 2 TMEM accumulators (2 x 128 columns).
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error code in *err, drains its own TMA and MMA work, frees its
 // TMEM and returns.
@@ -47,17 +46,16 @@ constexpr int BK = 64;      // k per chunk (one 128-byte bf16 row)
 constexpr uint32_t kStage = 65536;   // M_hi 16K | M_lo 16K | X_hi 16K | X_lo 16K
 constexpr uint32_t kEpiWarp = 32 * 33 * 4;
 
-// Launch shape per epilogue kind.  The plain product (TMA-store epilogue) is
-// bound by the operand stream: 8 epilogue warps and 3 smem stages.  Fused
-// epilogues read and write several more tensors per element, so their time
-// goes into the epilogue's global loads: 16 epilogue warps (twice the loads in
-// flight) and 2 stages, which is all the shared memory then leaves.
-// Each accumulator tile is 4 TMEM lane quarters x 4 groups of 16 r columns;
-// an epilogue warp owns quarter warp % 4 and 16 / nepi of the groups.
+// Launch shape of the fused-epilogue kernel.  The epilogues read and write
+// several tensors per element besides the product, so their time goes into the
+// epilogue's global loads: 16 epilogue warps (each owning one 16-column group
+// of a TMEM lane quarter; an accumulator tile is 4 lane quarters x 4 groups of
+// 16 r columns) and 2 smem stages, which is all the shared memory then leaves.
+// (The plain product, b3_plain.cuh, streams its operands differently.)
 template <class Epi>
 struct Cfg {
-  static constexpr int kEpi = Epi::kTmaStore ? 8 : 16;
-  static constexpr int kStages = Epi::kTmaStore ? 3 : 2;
+  static constexpr int kEpi = 16;
+  static constexpr int kStages = 2;
   static constexpr int kThreads = 32 * (2 + kEpi);
   static constexpr int kGroups = 16 / kEpi;   // 16-column groups per epilogue warp
   static constexpr uint32_t kOffEpi = kStages * kStage;
@@ -179,16 +177,13 @@ __device__ __forceinline__ uint32_t split_pair(float a, float b, uint32_t& lo) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Epilogue functor interface (b3_epilogues.cuh): either kTmaStore (the
-// product is stored split through tm_yhi / tm_ylo, no functor call), or a
-// batched two-phase functor: load(q, i, r, in) for kBatch elements, then
-// store(q, i, r, re, im, in) for each, so that the operand loads of a batch
-// are in flight together.
+// Epilogue functor interface (b3_epilogues.cuh): a batched two-phase functor,
+// load(q, i, r, in) for kBatch elements, then store(q, i, r, re, im, in) for
+// each, so that the operand loads of a batch are in flight together.
 template <class Epi>
 __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
-                 const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                  const KParams kp, const Epi epi) {
   constexpr int NSTAGE = Cfg<Epi>::kStages;
   constexpr int NEPI = Cfg<Epi>::kEpi;
@@ -331,42 +326,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
 #pragma unroll
       for (int g2 = 0; g2 < NG; ++g2) {
         const int cc = half + (NEPI / 4) * g2;   // 16-column group: r = r0 + 16 cc + 0..15
-        if constexpr (Epi::kTmaStore) {
-          // four 32 x 16 bf16 boxes (re hi, re lo, im hi, im lo); row = this lane's i.
-          // The previous group's stores must have finished reading the box.
-          if (lane == 0) bulk_wait_read0();
-          __syncwarp();
-          uint32_t* box = reinterpret_cast<uint32_t*>(stg);
-#pragma unroll
-          for (int j = 0; j < 16; j += 8) {
-            uint4 rh, rl, ih, il;
-            rh.x = split_pair(__uint_as_float(vr[g2][j + 0]), __uint_as_float(vr[g2][j + 1]), rl.x);
-            rh.y = split_pair(__uint_as_float(vr[g2][j + 2]), __uint_as_float(vr[g2][j + 3]), rl.y);
-            rh.z = split_pair(__uint_as_float(vr[g2][j + 4]), __uint_as_float(vr[g2][j + 5]), rl.z);
-            rh.w = split_pair(__uint_as_float(vr[g2][j + 6]), __uint_as_float(vr[g2][j + 7]), rl.w);
-            ih.x = split_pair(__uint_as_float(vi[g2][j + 0]), __uint_as_float(vi[g2][j + 1]), il.x);
-            ih.y = split_pair(__uint_as_float(vi[g2][j + 2]), __uint_as_float(vi[g2][j + 3]), il.y);
-            ih.z = split_pair(__uint_as_float(vi[g2][j + 4]), __uint_as_float(vi[g2][j + 5]), il.z);
-            ih.w = split_pair(__uint_as_float(vi[g2][j + 6]), __uint_as_float(vi[g2][j + 7]), il.w);
-            const int w = lane * 8 + j / 2;   // 32-bit word of this row's 16 bf16
-            *reinterpret_cast<uint4*>(box + 0 * 256 + w) = rh;
-            *reinterpret_cast<uint4*>(box + 1 * 256 + w) = rl;
-            *reinterpret_cast<uint4*>(box + 2 * 256 + w) = ih;
-            *reinterpret_cast<uint4*>(box + 3 * 256 + w) = il;
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {
-            const int x = (int)(tile * BR + cc * 16);
-            const uint32_t sb = smem_u32(box);
-            tma_store_3d(&tm_yhi, sb + 0 * 1024, x, i_base, 0);
-            tma_store_3d(&tm_ylo, sb + 1 * 1024, x, i_base, 0);
-            tma_store_3d(&tm_yhi, sb + 2 * 1024, x, i_base, 1);
-            tma_store_3d(&tm_ylo, sb + 3 * 1024, x, i_base, 1);
-            bulk_commit();
-          }
-          __syncwarp();
-        } else {
+        {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             stg[lane * 33 + j] = __uint_as_float(vr[g2][j]);
@@ -430,9 +390,6 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     }
   }
 
-  if constexpr (Epi::kTmaStore) {
-    if (warp >= 2 && lane == 0) bulk_wait0();
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

@@ -26,6 +26,7 @@
 #include "adjoint.h"
 #include "b3_epilogues.cuh"
 #include "b3_kernel.cuh"
+#include "b3_plain.cuh"
 #include "engine.h"
 
 namespace fcgle {
@@ -213,7 +214,6 @@ class EngineB3 : public EngineBase {
     FCGLE_CUDA(cudaStreamSynchronize(st_));
     static bool attrs = false;
     if (!attrs) {
-      set_smem_attr<b3::EpiStoreSplit>();
       set_smem_attr<b3::EpiStoreSplitGen>();
       set_smem_attr<b3::EpiStoreF32>();
       set_smem_attr<b3::EpiScaleF>();
@@ -227,6 +227,8 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiLBDF2>();
       set_smem_attr<b3::EpiLawsonRK2>();
       set_smem_attr<b3::EpiStrang>();
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b3::kPlSmemBytes));
       attrs = true;
     }
   }
@@ -443,15 +445,39 @@ class EngineB3 : public EngineBase {
   void store_split(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, SplitOut out) {
     const long long R = P_ / s_.p[mu];
     if (R % 8 == 0)
-      launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplit{}, &out);
+      launch_plain(xh, xl, mu, fwd, out);
     else
       launch_mp(xh, xl, mu, fwd, b3::EpiStoreSplitGen{P32(), out});
   }
 
+  // plain mode product with split output (R % 8 == 0): separate operand rings
+  void launch_plain(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, SplitOut out) {
+    const Mat& m = mat_[mu][fwd ? 0 : 1];
+    const long long R = P_ / s_.p[mu];
+    if (R % 8 != 0) throw std::runtime_error("plain mode product needs R % 8 == 0");
+    CUtensorMap txh, txl;
+    encode_bf16(&txh, xh, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    encode_bf16(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    b3::KParams kp;
+    kp.R = R;
+    kp.p = s_.p[mu];
+    kp.m_blocks = m.m_pad / b3::BM;
+    kp.k_chunks = m.k_pad / b3::BK;
+    kp.tiles = (R + b3::BR - 1) / b3::BR;
+    kp.err = err_->ptr;
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    CUtensorMap tyh, tyl;
+    encode_bf16_out(&tyh, out.hi, (uint64_t)R, (uint64_t)s_.p[mu]);
+    encode_bf16_out(&tyl, out.lo, (uint64_t)R, (uint64_t)s_.p[mu]);
+    b3::mp_b3_plain_kernel<<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, tyh, tyl,
+                                                                             kp);
+    FCGLE_LAUNCHED(launches);
+  }
+
   // one mode product of direction mu on split input (xh, xl) with epilogue epi
   template <class Epi>
-  void launch_mp(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, const Epi& epi,
-                 const SplitOut* tma_out = nullptr) {
+  void launch_mp(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, bool fwd, const Epi& epi) {
     const Mat& m = mat_[mu][fwd ? 0 : 1];
     const long long R = P_ / s_.p[mu];
     CUtensorMap txh, txl;
@@ -466,14 +492,8 @@ class EngineB3 : public EngineBase {
     kp.err = err_->ptr;
     const long long units = kp.tiles * kp.m_blocks;
     const int grid = (int)std::min<long long>(units, num_sms());
-    CUtensorMap tyh = txh, tyl = txl;   // unused unless the epilogue stores through TMA
-    if (Epi::kTmaStore) {
-      if (!tma_out) throw std::runtime_error("TMA-store epilogue without an output");
-      encode_bf16_out(&tyh, tma_out->hi, (uint64_t)R, (uint64_t)s_.p[mu]);
-      encode_bf16_out(&tyl, tma_out->lo, (uint64_t)R, (uint64_t)s_.p[mu]);
-    }
     b3::mp_b3_kernel<Epi><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_>>>(
-        txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, epi);
+        txh, txl, m.tm_hi, m.tm_lo, kp, epi);
     FCGLE_LAUNCHED(launches);
   }
 
