@@ -33,6 +33,7 @@ BOXES = [(-10.0, 10.0)] * 3
 ALPHAS = [1.2, 1.5, 1.8]
 PARS = dict(nu=1.0, eta=0.5, gamma=1.0, kappa=1.0, zeta=0.5)
 TAU = 1e-3
+KROGSTAD_BYTES_PER_ELEM = 16 * 16 + 32 + 3 * 24 + 32 + 40 + 40 + 32   # 504 B per complex element
 METRIC = "DoF*steps/s"
 UNIT = "DoF*steps/s"
 
@@ -338,6 +339,13 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "mp_b3_plain_kernel (one 256^3 mode product, split in/out)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
                 "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
     del X, Y
+    # the whole step against HBM: algorithmic bytes per element of one Krogstad step
+    # (16 plain products x 16 B; EpiFhat 32, 3 x EpiStageD 24, EpiKrog2 32, EpiKrog3 40,
+    # EpiKrogFinal 40, EpiUpdateG 32) over the padded tensor
+    step_bytes = KROGSTAD_BYTES_PER_ELEM * P
+    step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
+    step_roof = {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(step_gbs / peak, 4), "floor_ms": round(step_bytes / (peak * 1e9) * 1e3, 4)}
 
     # ---- end to end through the C ABI with host buffers
     hin = torch.from_numpy(u0_np.astype(np.complex64)).pin_memory()
@@ -393,7 +401,7 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "setup_s": round(setup_s, 3)}
         line.update(extra)
         print(json.dumps(line))

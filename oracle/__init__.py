@@ -20,8 +20,11 @@ arXiv 2510.21394) and shares no code with the CUDA path:
                  (Eq. fKu_diag) and the Kronecker-product form of exp
                  (Eq. Neudeckerd), from numpy ``eigh`` of each D_mu.
 * ``schemes`` -- the time integrators written in their vector form (Sec. 4:
-                 Eqs. lbdf2-v, Strang, krogstad-v) plus the Lawson/ETD2RK
-                 readings listed in the design doc, on top of ``tensor``.
+                 Eqs. lbdf2-v, Strang, krogstad-v) plus Lawson-Euler,
+                 Heun-based Lawson-RK2 and Cox-Matthews ETD2RK (standard forms,
+                 stated in ``schemes``), on top of ``tensor``.
+* ``adjoint`` -- the discrete adjoint of the Lawson-RK2 step and the gradient
+                 of a final-time misfit.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (closed forms, mpmath, brute force,

@@ -12,9 +12,12 @@ Schemes (each step maps (t_n, u_n) -> u_{n+1}):
 * ``strang``   Strang splitting (Eq. Strang) with the exact nonlinear flow
                (Sec. 4) and exp(tau K); no source.
 * ``krogstad`` Krogstad's fourth-order exponential RK (Eq. krogstad-v).
-* ``lawson_euler``, ``lawson_rk2``, ``etd2rk``: not in the paper; the readings
-               stated in the design doc (Lawson-Euler, Heun-based Lawson, Cox-Matthews
-               ETD2RK).
+* ``lawson_euler``, ``lawson_rk2``, ``etd2rk``: not in the paper; standard
+               forms taken here: Lawson-Euler u' = e^{tau K}(u + tau g(t, u));
+               Heun-based Lawson k1 = g(t, u), v = e^{tau K}(u + tau k1),
+               u' = e^{tau K}(u + tau/2 k1) + tau/2 g(t + tau, v); Cox-Matthews
+               ETD2RK a = u + tau phi_1(tau K) f, u' = a + tau phi_2(tau K)
+               (g(t + tau, a) - g(t, u)), f = K u + g(t, u).
 
 Test infrastructure only (see ``oracle/__init__``).
 """
