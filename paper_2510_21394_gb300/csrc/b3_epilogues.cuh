@@ -520,7 +520,8 @@ struct EpiKrog3 {
 };
 
 // Krogstad final combination, D^_4 = product, z = tau Lam:
-// S = W + tau (4 phi_3 - phi_2) D^_4 -> split;  U^ += S
+// S = W + tau (4 phi_3 - phi_2) D^_4;  U^ += S, and U^_{n+1} -> split (the
+// backward Tucker operator then gives u_{n+1} itself)
 struct EpiKrogFinal {
   FCGLE_EPI(4, 2)
   uint32_t P;
@@ -551,13 +552,15 @@ struct EpiKrogFinal {
       ur[v] = in[2][v] + sr[v];
       ui[v] = in[3][v] + si[v];
     }
-    put_csplit<V>(S, P, q, sr, si);
+    put_csplit<V>(S, P, q, ur, ui);
     stv<V>(Uh + q, ur);
     stv<V>(Uh + P + q, ui);
   }
 };
 
-// ETD2RK second stage, D^ = product, z = tau Lam: S = tau phi_2(z) D^ -> split;  U^ += S
+// ETD2RK second stage, D^ = product, z = tau Lam: U^ += tau phi_2(z) D^, and the
+// new spectral state U^_{n+1} -> split (the backward Tucker operator then gives
+// u_{n+1} itself, so the physical state carries the error of one transform)
 struct EpiEtd2 {
   FCGLE_EPI(2, 4)
   uint32_t P;
@@ -584,23 +587,153 @@ struct EpiEtd2 {
       ur[v] = in[0][v] + sr[v];
       ui[v] = in[1][v] + si[v];
     }
-    put_csplit<V>(S, P, q, sr, si);
+    put_csplit<V>(S, P, q, ur, ui);
     stv<V>(Uh + q, ur);
     stv<V>(Uh + P + q, ui);
   }
 };
 
-// LBDF2 (Eq. lbdf2-v): u_{n+1} = product -> U, u_n -> Uprev;
-// next right-hand side 4/3 u_{n+1} - 1/3 u_n + 2 tau/3 g(t_{n+2}, 2 u_{n+1} - u_n) -> split
-struct EpiLBDF2 {
-  FCGLE_EPI(2, 2)
+// phi_1(z) = (e^z - 1)/z: Horner form of sum_m z^m/(m+1)! for |z| < 1.5 (16 terms),
+// the quotient otherwise.  e^z - 1 = z phi_1(z) then carries no cancellation.
+__device__ __forceinline__ void phi1f(float zr, float zi, float& fr, float& fi) {
+  if (zr * zr + zi * zi < 2.25f) {
+    float ar = 1.f, ai = 0.f;
+    for (int m = 16; m >= 1; --m) {
+      const float w = 1.f / (float)(m + 1);
+      const float tr = 1.f + w * (ar * zr - ai * zi);
+      ai = w * (ar * zi + ai * zr);
+      ar = tr;
+    }
+    fr = ar;
+    fi = ai;
+  } else {
+    float sn, co;
+    sincosf(zi, &sn, &co);
+    const float ex = expf(zr);
+    const float er = ex * co - 1.f, ei = ex * sn;
+    const float inv = 1.f / (zr * zr + zi * zi);
+    fr = (er * zr + ei * zi) * inv;
+    fi = (ei * zr - er * zi) * inv;
+  }
+}
+
+// The schemes below keep the spectral state U^ = Q^T u (FP32) as the primary
+// state: each step updates U^ in spectral space, and the backward Tucker
+// operator of U^_{n+1} gives u_{n+1}.  The physical state then carries the
+// error of one split-BF16 transform instead of one per step.
+
+// Linearly-implicit Euler (kind 0, Eq. lbdf2-v first step) and Lawson-Euler
+// (kind 1): product = G^ = fwd(g(t_n, u_n)), z = tau Lam, f = 1/(1 - z) or e^z:
+// U^ <- U^ + (f - 1) U^ + tau f G^, with f - 1 = z f resp. z phi_1(z) (no
+// cancellation); U^_{n+1} -> Uh and -> split.
+struct EpiSpecStep {
+  FCGLE_EPI(2, 4)
+  uint32_t P;
+  LamF L;
+  float* Uh;
+  int kind;
+  float tau;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
+    ldv<V>(Uh + q, in[0]);
+    ldv<V>(Uh + P + q, in[1]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[2][V]) const {
+    float lr[V], li[V], ur[V], ui[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float zr = tau * lr[v], zi = tau * li[v];
+      float fr, fi, mr, mi;   // f and f - 1
+      if (kind == 0) {
+        const float ar = 1.f - zr, ai = -zi, inv = 1.f / (ar * ar + ai * ai);
+        fr = ar * inv;
+        fi = -ai * inv;
+        mr = zr * fr - zi * fi;
+        mi = zr * fi + zi * fr;
+      } else {
+        float pr, pi;
+        phi1f(zr, zi, pr, pi);
+        mr = zr * pr - zi * pi;
+        mi = zr * pi + zi * pr;
+        fr = 1.f + mr;
+        fi = mi;
+      }
+      const float xr = in[0][v], xi = in[1][v];
+      ur[v] = xr + (mr * xr - mi * xi) + tau * (fr * re[v] - fi * im[v]);
+      ui[v] = xi + (mr * xi + mi * xr) + tau * (fr * im[v] + fi * re[v]);
+    }
+    stv<V>(Uh + q, ur);
+    stv<V>(Uh + P + q, ui);
+    put_csplit<V>(S, P, q, ur, ui);
+  }
+};
+
+// LBDF2 (Eq. lbdf2-v) in the spectral state: product = G^_e = fwd(g(t_{n+1},
+// 2 u_n - u_{n-1})), z = theta Lam, theta = 2 tau / 3; with dU^_n = U^_n - U^_{n-1}
+// the step (1 - z) U^_{n+1} = 4/3 U^_n - 1/3 U^_{n-1} + theta G^_e reads
+// dU^_{n+1} = (1 - z)^{-1} (dU^_n / 3 + z U^_n + theta G^_e).
+// third = 0 and theta = tau give the linearly-implicit Euler first step.
+// dU^_{n+1} -> dU, U^_{n+1} -> Uh and -> split.
+struct EpiLBDF2S {
+  FCGLE_EPI(4, 2)
+  uint32_t P;
+  LamF L;
+  float* Uh;
+  float* dU;
+  float theta;
+  float third;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
+    ldv<V>(Uh + q, in[0]);
+    ldv<V>(Uh + P + q, in[1]);
+    if (third != 0.f) {
+      ldv<V>(dU + q, in[2]);
+      ldv<V>(dU + P + q, in[3]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) in[2][v] = in[3][v] = 0.f;
+    }
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[4][V]) const {
+    float lr[V], li[V], dr[V], di[V], ur[V], ui[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float zr = theta * lr[v], zi = theta * li[v];
+      const float ar = 1.f - zr, ai = -zi, inv = 1.f / (ar * ar + ai * ai);
+      const float fr = ar * inv, fi = -ai * inv;   // (1 - z)^{-1}
+      const float xr = in[0][v], xi = in[1][v];
+      const float br = third * in[2][v] + (zr * xr - zi * xi) + theta * re[v];
+      const float bi = third * in[3][v] + (zr * xi + zi * xr) + theta * im[v];
+      dr[v] = fr * br - fi * bi;
+      di[v] = fr * bi + fi * br;
+      ur[v] = xr + dr[v];
+      ui[v] = xi + di[v];
+    }
+    stv<V>(dU + q, dr);
+    stv<V>(dU + P + q, di);
+    stv<V>(Uh + q, ur);
+    stv<V>(Uh + P + q, ui);
+    put_csplit<V>(S, P, q, ur, ui);
+  }
+};
+
+// LBDF2 backward epilogue: u_{n+1} = product -> U (u_n read from U first);
+// g(t, 2 u_{n+1} - u_n) -> split, the input of the next step's forward operator
+struct EpiExtrapG {
+  FCGLE_EPI(2, 4)
   uint32_t P;
   float* U;
-  float* Uprev;
   GStatic g;
   GTime t;
-  float tau;
-  SplitOut Vout;
+  SplitOut S;
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
     ldv<V>(U + q, in[0]);
@@ -609,69 +742,90 @@ struct EpiLBDF2 {
   template <int V>
   __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
                         const float (&in)[2][V]) const {
-    stv<V>(Uprev + q, in[0]);
-    stv<V>(Uprev + P + q, in[1]);
-    stv<V>(U + q, re);
-    stv<V>(U + P + q, im);
     float er[V], ei[V], gr[V], gi[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       er[v] = 2.f * re[v] - in[0][v];
       ei[v] = 2.f * im[v] - in[1][v];
     }
+    stv<V>(U + q, re);
+    stv<V>(U + P + q, im);
     g_eval<V>(g, t, P, q, er, ei, gr, gi);
-    const float c = 2.f * tau / 3.f;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      er[v] = (4.f * re[v] - in[0][v]) / 3.f + c * gr[v];
-      ei[v] = (4.f * im[v] - in[1][v]) / 3.f + c * gi[v];
-    }
-    put_csplit<V>(Vout, P, q, er, ei);
+    put_csplit<V>(S, P, q, gr, gi);
   }
 };
 
-// Lawson-RK2 (Heun): u_{n+1} = product + tau/2 g(t_{n+1}, EA) -> U;
-// next k1 = g(t_{n+1}, u_{n+1}); A = u + tau k1, B = u + tau/2 k1 -> split
-struct EpiLawsonRK2 {
-  FCGLE_EPI(2, 2)
+// Lawson-RK2 (Heun) in the spectral state, first forward epilogue:
+// product = K^_1 = fwd(g(t_n, u_n)), z = tau Lam, e^z = 1 + z phi_1(z):
+// V^ = e^z (U^ + tau K^_1) -> split (v = bwd(V^) is the Heun predictor),
+// W^ = e^z (U^ + tau/2 K^_1) -> W (FP32)
+struct EpiLRK2A {
+  FCGLE_EPI(2, 4)
   uint32_t P;
-  float* U;
-  const float* EA;
-  GStatic g;
-  GTime t;   // t_{n+1}
+  LamF L;
+  const float* Uh;
+  float* W;
   float tau;
-  SplitOut A, Bv;
+  SplitOut S;
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
-    ldv_ro<V>(EA + q, in[0]);
-    ldv_ro<V>(EA + P + q, in[1]);
+    ldv_ro<V>(Uh + q, in[0]);
+    ldv_ro<V>(Uh + P + q, in[1]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[2][V]) const {
+    float lr[V], li[V], vr[V], vi[V], wr[V], wi[V];
+    lam_eval<V>(L, i, r, lr, li);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float zr = tau * lr[v], zi = tau * li[v];
+      float pr, pi;
+      phi1f(zr, zi, pr, pi);
+      const float mr = zr * pr - zi * pi, mi = zr * pi + zi * pr;   // e^z - 1
+      const float fr = 1.f + mr, fi = mi;                           // e^z
+      const float xr = in[0][v], xi = in[1][v];
+      const float br = xr + (mr * xr - mi * xi), bi = xi + (mr * xi + mi * xr);   // e^z U^
+      const float kr = fr * re[v] - fi * im[v], ki = fr * im[v] + fi * re[v];     // e^z K^_1
+      vr[v] = br + tau * kr;
+      vi[v] = bi + tau * ki;
+      wr[v] = br + 0.5f * tau * kr;
+      wi[v] = bi + 0.5f * tau * ki;
+    }
+    put_csplit<V>(S, P, q, vr, vi);
+    stv<V>(W + q, wr);
+    stv<V>(W + P + q, wi);
+  }
+};
+
+// Lawson-RK2 second forward epilogue: product = fwd(g(t_{n+1}, v)):
+// U^_{n+1} = W^ + tau/2 product -> Uh and -> split
+struct EpiLRK2B {
+  FCGLE_EPI(2, 4)
+  uint32_t P;
+  const float* W;
+  float* Uh;
+  float tau;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
+    ldv_ro<V>(W + q, in[0]);
+    ldv_ro<V>(W + P + q, in[1]);
   }
   template <int V>
   __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
                         const float (&in)[2][V]) const {
-    float gr[V], gi[V], ur[V], ui[V];
-    g_eval<V>(g, t, P, q, in[0], in[1], gr, gi);
+    float ur[V], ui[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      ur[v] = re[v] + 0.5f * tau * gr[v];
-      ui[v] = im[v] + 0.5f * tau * gi[v];
+      ur[v] = in[0][v] + 0.5f * tau * re[v];
+      ui[v] = in[1][v] + 0.5f * tau * im[v];
     }
-    stv<V>(U + q, ur);
-    stv<V>(U + P + q, ui);
-    g_eval<V>(g, t, P, q, ur, ui, gr, gi);
-    float ar[V], ai[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      ar[v] = ur[v] + tau * gr[v];
-      ai[v] = ui[v] + tau * gi[v];
-      ur[v] += 0.5f * tau * gr[v];
-      ui[v] += 0.5f * tau * gi[v];
-    }
-    put_csplit<V>(A, P, q, ar, ai);
-    put_csplit<V>(Bv, P, q, ur, ui);
+    stv<V>(Uh + q, ur);
+    stv<V>(Uh + P + q, ui);
+    put_csplit<V>(S, P, q, ur, ui);
   }
 };
-
 // Exact flow of w' = gamma w - (kappa + i zeta)|w|^2 w over time t (Sec. 4):
 // w(t) = exp(t gamma - (kappa + i zeta)/(2 kappa) log(1 + 2 t phi_1(2 gamma t) kappa |w0|^2)) w0
 struct Flow {

@@ -224,8 +224,11 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiKrog3>();
       set_smem_attr<b3::EpiKrogFinal>();
       set_smem_attr<b3::EpiEtd2>();
-      set_smem_attr<b3::EpiLBDF2>();
-      set_smem_attr<b3::EpiLawsonRK2>();
+      set_smem_attr<b3::EpiSpecStep>();
+      set_smem_attr<b3::EpiLBDF2S>();
+      set_smem_attr<b3::EpiExtrapG>();
+      set_smem_attr<b3::EpiLRK2A>();
+      set_smem_attr<b3::EpiLRK2B>();
       set_smem_attr<b3::EpiStrang>();
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
@@ -569,26 +572,23 @@ class EngineB3 : public EngineBase {
     rs_tau_ = tau;
     rs_t0_ = t0;
     float* U = F32(kU);
-    SplitOut V = SP(kV), W = SP(kW);
+    SplitOut V = SP(kV);
     const float ft = (float)tau;
     switch (scheme) {
-      case FCGLE_LIE:
-      case FCGLE_LAWSON_EULER:
-      case FCGLE_LBDF2:
-        gsplit(U, t0, 1.f, ft, V);   // V = u_0 + tau g(t_0, u_0)
-        break;
       case FCGLE_STRANG:
         flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(tau / 2), U, V);
         FCGLE_LAUNCHED(launches);
         break;
+      case FCGLE_LIE:
+      case FCGLE_LAWSON_EULER:
+      case FCGLE_LBDF2:
       case FCGLE_LAWSON_RK2:
-        gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, W);   // A = u + tau k1, B = u + tau/2 k1
-        break;
       case FCGLE_ETD2RK:
       case FCGLE_KROGSTAD:
-        gsplit(U, t0, 1.f, 0.f, V);                     // U^_0 = fwd(u_0)
+        // the spectral state U^_0 = fwd(u_0) is carried from here on; V = g(t_0, u_0)
+        gsplit(U, t0, 1.f, 0.f, V);
         tucker(V, true, b3::EpiStoreF32{P32(), F32(kUh)});
-        gsplit(U, t0, 0.f, 1.f, V);                     // G_0
+        gsplit(U, t0, 0.f, 1.f, V);
         break;
       default: throw InvalidArg("unknown scheme");
     }
@@ -599,14 +599,15 @@ class EngineB3 : public EngineBase {
     const int scheme = rs_scheme_;
     const double tau = rs_tau_, t0 = rs_t0_, t = t0 + n * tau;
     float* U = F32(kU);
-    SplitOut V = SP(kV), W = SP(kW);
+    SplitOut V = SP(kV);
     const float ft = (float)tau;
     switch (scheme) {
       case FCGLE_LIE:
       case FCGLE_LAWSON_EULER: {
-        const int kind = scheme == FCGLE_LIE ? 0 : 1;   // (1 - tau lam)^{-1} or e^{tau lam}
-        tucker(V, true, b3::EpiScaleF{P32(), lf_, kind, ft, V});
-        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 1.f, ft, V});
+        // U^ <- f(tau Lam)(U^ + tau G^), f = 1/(1 - z) or e^z;  u_{n+1} = bwd(U^);  V = g(t_{n+1}, u_{n+1})
+        const int kind = scheme == FCGLE_LIE ? 0 : 1;
+        tucker(V, true, b3::EpiSpecStep{P32(), lf_, F32(kUh), kind, ft, V});
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
       }
       case FCGLE_STRANG: {
@@ -615,31 +616,34 @@ class EngineB3 : public EngineBase {
         break;
       }
       case FCGLE_LAWSON_RK2: {
-        float* EA = F32(kEA);
-        tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
-        tucker(V, false, b3::EpiStoreF32{P32(), EA});
-        tucker(W, true, b3::EpiScaleF{P32(), lf_, 1, ft, W});
-        tucker(W, false, b3::EpiLawsonRK2{P32(), U, EA, gs_, gtime(t + tau), ft, V, W});
+        float *Uh = F32(kUh), *Wh = F32(kEA);
+        // V^ = e^z (U^ + tau K^_1) -> v = bwd(V^);  W^ = e^z (U^ + tau/2 K^_1)
+        tucker(V, true, b3::EpiLRK2A{P32(), lf_, Uh, Wh, ft, V});
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
+        // U^_{n+1} = W^ + tau/2 fwd(g(t_{n+1}, v));  u_{n+1} = bwd(U^_{n+1})
+        tucker(V, true, b3::EpiLRK2B{P32(), Wh, Uh, ft, V});
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
       }
       case FCGLE_LBDF2: {
-        // step 0 is linearly-implicit Euler (Eq. lbdf2-v); its epilogue keeps u_0
-        // as u_{n-1} and forms the first LBDF2 right-hand side
-        const float th = n == 0 ? ft : (float)(2.0 * tau / 3.0);
-        tucker(V, true, b3::EpiScaleF{P32(), lf_, 0, th, V});
-        tucker(V, false, b3::EpiLBDF2{P32(), U, F32(kUp), gs_, gtime(t + 2 * tau), ft, V});
+        // step 0 is linearly-implicit Euler (Eq. lbdf2-v); later steps the LBDF2
+        // update of the spectral state with dU^ = U^_n - U^_{n-1}
+        const bool first = n == 0;
+        const float th = first ? ft : (float)(2.0 * tau / 3.0);
+        tucker(V, true, b3::EpiLBDF2S{P32(), lf_, F32(kUh), F32(kUp), th, first ? 0.f : 1.f / 3.f, V});
+        tucker(V, false, b3::EpiExtrapG{P32(), U, gs_, gtime(t + 2 * tau), V});
         break;
       }
       case FCGLE_ETD2RK: {
         float *Uh = F32(kUh), *Fh = F32(kFh);
         // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
         tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V});
-        // a = u + bwd(S1) -> U;  D = g(t + tau, a) - g(t, u)
-        tucker(V, false, b3::EpiStageD{P32(), U, U, gs_, gtime(t + tau), gtime(t), V});
-        // S2 = tau phi_2(tau Lam) o D^;  U^ += S2
+        // a = u + bwd(S1);  D = g(t + tau, a) - g(t, u)
+        tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, gtime(t + tau), gtime(t), V});
+        // U^_{n+1} = a^ + tau phi_2(tau Lam) o D^
         tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V});
-        // u_{n+1} = a + bwd(S2);  next G = g(t + tau, u_{n+1})
-        tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, gtime(t + tau), 0.f, 1.f, V});
+        // u_{n+1} = bwd(U^_{n+1});  next G = g(t + tau, u_{n+1})
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
       }
       case FCGLE_KROGSTAD: {
@@ -655,10 +659,10 @@ class EngineB3 : public EngineBase {
         // D^_3;  S = tau (phi_1 F^ + 2 phi_2 D^_3);  W = part of the final combination
         tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V});
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
-        // D^_4;  S = W + tau (4 phi_3 - phi_2) D^_4;  U^ += S
+        // D^_4;  U^_{n+1} = U^ + W + tau (4 phi_3 - phi_2) D^_4
         tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V});
-        // u_{n+1} = u + bwd(S);  next G = g(t + tau, u_{n+1})
-        tucker(V, false, b3::EpiUpdateG{P32(), U, 1, gs_, t1, 0.f, 1.f, V});
+        // u_{n+1} = bwd(U^_{n+1});  next G = g(t + tau, u_{n+1})
+        tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, t1, 0.f, 1.f, V});
         break;
       }
       default: throw InvalidArg("unknown scheme");
