@@ -622,17 +622,19 @@ __device__ __forceinline__ void phi1f(float zr, float zi, float& fr, float& fi) 
 // operator of U^_{n+1} gives u_{n+1}.  The physical state then carries the
 // error of one split-BF16 transform instead of one per step.
 
-// Linearly-implicit Euler (kind 0, Eq. lbdf2-v first step) and Lawson-Euler
-// (kind 1): product = G^ = fwd(g(t_n, u_n)), z = tau Lam, f = 1/(1 - z) or e^z:
-// U^ <- U^ + (f - 1) U^ + tau f G^, with f - 1 = z f resp. z phi_1(z) (no
-// cancellation); U^_{n+1} -> Uh and -> split.
+// Linearly-implicit Euler (kind 0, Eq. lbdf2-v first step), Lawson-Euler
+// (kind 1, c = tau) and the linear part of Strang (kind 1, c = 1):
+// product = X^ (fwd(g(t_n, u_n)), resp. the flow increment), z = theta Lam,
+// f = 1/(1 - z) or e^z:  U^ <- U^ + (f - 1) U^ + c f X^, with f - 1 = z f
+// resp. z phi_1(z) (no cancellation); U^_{n+1} -> Uh and -> split.
 struct EpiSpecStep {
   FCGLE_EPI(2, 4)
   uint32_t P;
   LamF L;
   float* Uh;
   int kind;
-  float tau;
+  float theta;
+  float c;
   SplitOut S;
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
@@ -646,7 +648,7 @@ struct EpiSpecStep {
     lam_eval<V>(L, i, r, lr, li);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const float zr = tau * lr[v], zi = tau * li[v];
+      const float zr = theta * lr[v], zi = theta * li[v];
       float fr, fi, mr, mi;   // f and f - 1
       if (kind == 0) {
         const float ar = 1.f - zr, ai = -zi, inv = 1.f / (ar * ar + ai * ai);
@@ -663,8 +665,8 @@ struct EpiSpecStep {
         fi = mi;
       }
       const float xr = in[0][v], xi = in[1][v];
-      ur[v] = xr + (mr * xr - mi * xi) + tau * (fr * re[v] - fi * im[v]);
-      ui[v] = xi + (mr * xi + mi * xr) + tau * (fr * im[v] + fi * re[v]);
+      ur[v] = xr + (mr * xr - mi * xi) + c * (fr * re[v] - fi * im[v]);
+      ui[v] = xi + (mr * xi + mi * xr) + c * (fr * im[v] + fi * re[v]);
     }
     stv<V>(Uh + q, ur);
     stv<V>(Uh + P + q, ui);
@@ -842,27 +844,45 @@ __device__ __forceinline__ void flow_eval(const Flow& f, float wr, float wi, flo
   yi = m * (c * wi + s * wr);
 }
 
-// Strang (Eq. Strang): u_{n+1} = Phi(product) -> U;  next V = Phi(u_{n+1}) -> split
-struct EpiStrang {
+// Phi_t(w) - w = (e^E - 1) w with E = t gamma - (1 + i zeta/kappa) L / 2,
+// L = log(1 + c2 |w|^2): e^E - 1 = expm1(Re E) cos(Im E) - 2 sin^2(Im E / 2)
+// + i e^{Re E} sin(Im E), without cancellation for small t.
+__device__ __forceinline__ void flow_incr(const Flow& f, float wr, float wi, float& dr, float& di) {
+  const float L = log1pf(f.c2 * (wr * wr + wi * wi));
+  const float a = f.gamma_t - 0.5f * L, b = -f.zk * L;
+  float s, c, sh, ch;
+  sincosf(b, &s, &c);
+  sincosf(0.5f * b, &sh, &ch);
+  const float em = expm1f(a);
+  const float er = em * c - 2.f * sh * sh, ei = (1.f + em) * s;
+  dr = er * wr - ei * wi;
+  di = er * wi + ei * wr;
+}
+
+// Strang (Eq. Strang) with the spectral state e^ = Q^T w, w the state after
+// the linear flow: u_{n+1} = Phi_{tau/2}(w) with w = product -> U, and the
+// increment Phi_tau(w) - w -> split, which the next step's forward operator
+// turns into e^ <- e^{tau Lam}(e^ + fwd(Phi_tau(w) - w)) (EpiSpecStep, c = 1).
+struct EpiStrangB {
   FCGLE_EPI(0, 4)
   uint32_t P;
   float* U;
-  Flow f;
-  SplitOut Vout;
+  Flow half, full;
+  SplitOut S;
   template <int V>
   __device__ void load(uint32_t, int, uint32_t, float (&)[1][V]) const {}
   template <int V>
   __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
                         const float (&)[1][V]) const {
-    float ur[V], ui[V], vr[V], vi[V];
+    float ur[V], ui[V], dr[V], di[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      flow_eval(f, re[v], im[v], ur[v], ui[v]);
-      flow_eval(f, ur[v], ui[v], vr[v], vi[v]);
+      flow_eval(half, re[v], im[v], ur[v], ui[v]);
+      flow_incr(full, re[v], im[v], dr[v], di[v]);
     }
     stv<V>(U + q, ur);
     stv<V>(U + P + q, ui);
-    put_csplit<V>(Vout, P, q, vr, vi);
+    put_csplit<V>(S, P, q, dr, di);
   }
 };
 

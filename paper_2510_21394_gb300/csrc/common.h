@@ -119,6 +119,8 @@ void sumsq(const Shape& s, const T* X, double* out_dev, cudaStream_t st, long lo
 // FP64, complex matrix: Y[c'][i][r] = sum_{c,k} B[(c',i)][(c,k)] X[c][r][k], B 2p x 2p.
 void mp_f64(const double* X, double* Y, const double* M, int p, size_t R, bool cplx,
             cudaStream_t st, long long& nl);
+// FP32 real mu-mode product (same layout and kernel as mp_f64, REAL mode)
+void mp_f32(const float* X, float* Y, const float* M, int p, size_t R, cudaStream_t st, long long& nl);
 
 // ------------------------------------------------------------ host setup
 // FP64 symmetric eigendecomposition A = Z diag(w) Z^T (A row-major n x n).

@@ -123,13 +123,27 @@ __global__ void gsplit_kernel(uint32_t P, b3::GStatic g, b3::GTime t, const floa
 }
 
 // V = Phi_t(u) (split)
-__global__ void flow_split_kernel(uint32_t P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
+// U = Phi_t(W)
+__global__ void flow_kernel(uint32_t P, b3::Flow f, const float* __restrict__ W, float* __restrict__ U) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    float wr[4], wi[4], ur[4], ui[4];
+    b3::ldv<4>(W + q, wr);
+    b3::ldv<4>(W + P + q, wi);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) b3::flow_eval(f, wr[v], wi[v], ur[v], ui[v]);
+    b3::stv<4>(U + q, ur);
+    b3::stv<4>(U + P + q, ui);
+  }
+}
+
+// V = Phi_t(u) - u -> split (Strang's first half step as an increment)
+__global__ void flow_incr_split_kernel(uint32_t P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
   for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
     float ur[4], ui[4], vr[4], vi[4];
     b3::ldv<4>(U + q, ur);
     b3::ldv<4>(U + P + q, ui);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) b3::flow_eval(f, ur[v], ui[v], vr[v], vi[v]);
+    for (int v = 0; v < 4; ++v) b3::flow_incr(f, ur[v], ui[v], vr[v], vi[v]);
     b3::put_csplit<4>(V, P, q, vr, vi);
   }
 }
@@ -229,7 +243,7 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiExtrapG>();
       set_smem_attr<b3::EpiLRK2A>();
       set_smem_attr<b3::EpiLRK2B>();
-      set_smem_attr<b3::EpiStrang>();
+      set_smem_attr<b3::EpiStrangB>();
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
       attrs = true;
@@ -241,6 +255,7 @@ class EngineB3 : public EngineBase {
       for (int f = 0; f < 2; ++f) {
         if (mat_[mu][f].hi) cudaFree(mat_[mu][f].hi);
         if (mat_[mu][f].lo) cudaFree(mat_[mu][f].lo);
+        if (mat_[mu][f].f32) cudaFree(mat_[mu][f].f32);
       }
   }
 
@@ -409,6 +424,7 @@ class EngineB3 : public EngineBase {
   struct Mat {
     __nv_bfloat16* hi = nullptr;
     __nv_bfloat16* lo = nullptr;
+    float* f32 = nullptr;   // p x p, for the FP32 transforms at the ends of a time integration
     int p = 0, m_pad = 0, k_pad = 0;
     CUtensorMap tm_hi, tm_lo;
   };
@@ -442,6 +458,23 @@ class EngineB3 : public EngineBase {
     FCGLE_CUDA(cudaMemcpy(m.lo, lo.data(), bytes, cudaMemcpyHostToDevice));
     encode_bf16(&m.tm_hi, m.hi, m.k_pad, m.m_pad, b3::BM);
     encode_bf16(&m.tm_lo, m.lo, m.k_pad, m.m_pad, b3::BM);
+    std::vector<float> f((size_t)p * p);
+    for (size_t e = 0; e < f.size(); ++e) f[e] = (float)M[e];
+    FCGLE_CUDA(cudaMalloc(&m.f32, f.size() * 4));
+    FCGLE_CUDA(cudaMemcpy(m.f32, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  }
+
+  // Tucker operator in FP32 on the CUDA cores (X, Y planar FP32, distinct);
+  // used where the split-BF16 error must not enter: U^_0 = fwd(u_0) at the
+  // start of a time integration and u(T) = bwd(U^_T) at its end.
+  void tucker_f32(const float* X, float* Y, bool fwd) {
+    float* tmp[2] = {F32(kFh), F32(kD2)};
+    const float* src = X;
+    for (int mu = 0; mu < s_.d; ++mu) {
+      float* dst = mu == s_.d - 1 ? Y : tmp[mu % 2];
+      mp_f32(src, dst, mat_[mu][fwd ? 0 : 1].f32, s_.p[mu], (size_t)(P_ / s_.p[mu]), st_, launches);
+      src = dst;
+    }
   }
 
   // mode product with a split output: TMA stores when the output rows allow
@@ -564,6 +597,20 @@ class EngineB3 : public EngineBase {
     if (nsteps == 0) return;
     begin(scheme, tau, t0);
     for (int n = 0; n < nsteps; ++n) step(n);
+    finish();
+  }
+
+  // u(T) from the carried spectral state by the FP32 backward operator (Strang:
+  // u(T) = Phi_{tau/2}(bwd(e^))), replacing the split-BF16 one of the last step
+  void finish() {
+    if (rs_scheme_ == FCGLE_STRANG) {
+      float* W = F32(kWork);
+      tucker_f32(F32(kUh), W, false);
+      flow_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(rs_tau_ / 2), W, F32(kU));
+      FCGLE_LAUNCHED(launches);
+    } else {
+      tucker_f32(F32(kUh), F32(kU), false);
+    }
   }
 
   // entry state of the loop from u_0 in F32(kU)
@@ -576,7 +623,9 @@ class EngineB3 : public EngineBase {
     const float ft = (float)tau;
     switch (scheme) {
       case FCGLE_STRANG:
-        flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(tau / 2), U, V);
+        // e^_0 = fwd(u_0) (FP32); V = Phi_{tau/2}(u_0) - u_0
+        tucker_f32(U, F32(kUh), true);
+        flow_incr_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(tau / 2), U, V);
         FCGLE_LAUNCHED(launches);
         break;
       case FCGLE_LIE:
@@ -585,9 +634,8 @@ class EngineB3 : public EngineBase {
       case FCGLE_LAWSON_RK2:
       case FCGLE_ETD2RK:
       case FCGLE_KROGSTAD:
-        // the spectral state U^_0 = fwd(u_0) is carried from here on; V = g(t_0, u_0)
-        gsplit(U, t0, 1.f, 0.f, V);
-        tucker(V, true, b3::EpiStoreF32{P32(), F32(kUh)});
+        // the spectral state U^_0 = fwd(u_0) (FP32) is carried from here on; V = g(t_0, u_0)
+        tucker_f32(U, F32(kUh), true);
         gsplit(U, t0, 0.f, 1.f, V);
         break;
       default: throw InvalidArg("unknown scheme");
@@ -606,13 +654,15 @@ class EngineB3 : public EngineBase {
       case FCGLE_LAWSON_EULER: {
         // U^ <- f(tau Lam)(U^ + tau G^), f = 1/(1 - z) or e^z;  u_{n+1} = bwd(U^);  V = g(t_{n+1}, u_{n+1})
         const int kind = scheme == FCGLE_LIE ? 0 : 1;
-        tucker(V, true, b3::EpiSpecStep{P32(), lf_, F32(kUh), kind, ft, V});
+        tucker(V, true, b3::EpiSpecStep{P32(), lf_, F32(kUh), kind, ft, ft, V});
         tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
       }
       case FCGLE_STRANG: {
-        tucker(V, true, b3::EpiScaleF{P32(), lf_, 1, ft, V});
-        tucker(V, false, b3::EpiStrang{P32(), U, flow(tau / 2), V});
+        // e^ <- e^{tau Lam}(e^ + fwd(increment));  w = bwd(e^);  u_{n+1} = Phi_{tau/2}(w);
+        // next increment Phi_tau(w) - w
+        tucker(V, true, b3::EpiSpecStep{P32(), lf_, F32(kUh), 1, ft, 1.f, V});
+        tucker(V, false, b3::EpiStrangB{P32(), U, flow(tau / 2), flow(tau), V});
         break;
       }
       case FCGLE_LAWSON_RK2: {
@@ -675,7 +725,10 @@ class EngineB3 : public EngineBase {
     begin(scheme, tau, t0);
   }
   void one_step(int n) override { step(n); }
-  void end_steps(void* uT) override { unpack_f32(F32(kU), (float*)uT); }
+  void end_steps(void* uT) override {
+    finish();
+    unpack_f32(F32(kU), (float*)uT);
+  }
   bool time_dependent() const override { return gs_.nsrc > 0; }
 
   int rs_scheme_ = 0;

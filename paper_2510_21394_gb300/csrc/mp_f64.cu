@@ -10,7 +10,10 @@
 //     A(r, (c, k)) = X[c][r][k];   Y[c'][i][r] = C[r][(c', i)].
 // GB300's FP64 rate is a small fraction of its tensor-core rate, so this
 // is a plain shared-memory tiled SIMT GEMM (64 x 64 tile, 4 x 4 per thread):
-// it is FP64-ALU bound by a wide margin at every size used here.
+// it is FP64-ALU bound by a wide margin at every size used here.  The same
+// kernel in FP32 (real matrices only) serves the split-BF16 engine for the
+// few transforms per solve that must not carry the split-BF16 error (the
+// first forward and the last backward Tucker operator of a time integration).
 #include "common.h"
 
 namespace fcgle {
@@ -19,11 +22,11 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-template <bool CPLX>
-__global__ void __launch_bounds__(NT) mp_f64_kernel(const double* __restrict__ X, double* __restrict__ Y,
-                                                    const double* __restrict__ B, int p, long long R) {
-  __shared__ double As[BK][BM + 2];
-  __shared__ double Bs[BK][BN + 2];
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(NT) mp_simt_kernel(const T* __restrict__ X, T* __restrict__ Y,
+                                                     const T* __restrict__ B, int p, long long R) {
+  __shared__ T As[BK][BM + 2];
+  __shared__ T Bs[BK][BN + 2];
   const long long rows = CPLX ? R : 2 * R;
   const int K = CPLX ? 2 * p : p;
   const int Ncol = CPLX ? 2 * p : p;
@@ -34,11 +37,11 @@ __global__ void __launch_bounds__(NT) mp_f64_kernel(const double* __restrict__ X
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;   // rows tx*4.., cols ty*4..
 
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
   const int lk = tid & 15, lr = tid >> 4;   // loader: k offset, row offset (+16 j)
   for (int k0 = 0; k0 < K; k0 += BK) {
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(NT) mp_f64_kernel(const double* __restrict__ X
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const long long row = row0 + lr + 16 * j;
-      double a = 0.0;
+      T a = T(0);
       if (row < rows && kk < K) {
         if (CPLX) {
           const int c = kk >= p ? 1 : 0;
@@ -57,12 +60,12 @@ __global__ void __launch_bounds__(NT) mp_f64_kernel(const double* __restrict__ X
       }
       As[lk][lr + 16 * j] = a;
       const int col = col0 + lr + 16 * j;
-      Bs[lk][lr + 16 * j] = (col < Ncol && kk < K) ? B[(long long)col * K + kk] : 0.0;
+      Bs[lk][lr + 16 * j] = (col < Ncol && kk < K) ? B[(long long)col * K + kk] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[k][tx * 4 + i];
 #pragma unroll
@@ -104,9 +107,16 @@ void mp_f64(const double* X, double* Y, const double* M, int p, size_t R, bool c
   const int ncol = cplx ? 2 * p : p;
   dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)((ncol + BN - 1) / BN));
   if (cplx)
-    mp_f64_kernel<true><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+    mp_simt_kernel<double, true><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
   else
-    mp_f64_kernel<false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+    mp_simt_kernel<double, false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+  FCGLE_LAUNCHED(nl);
+}
+
+void mp_f32(const float* X, float* Y, const float* M, int p, size_t R, cudaStream_t st, long long& nl) {
+  const long long rows = 2 * (long long)R;
+  dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)((p + BN - 1) / BN));
+  mp_simt_kernel<float, false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
   FCGLE_LAUNCHED(nl);
 }
 
