@@ -157,19 +157,19 @@ __device__ __forceinline__ void cmulv(const float (&ar)[V], const float (&ai)[V]
 }
 
 // ---------------------------------------------------- spectral scalars, FP32
-// phi_1, phi_2, phi_3 of z (Eq. phi).  |z| < 1.5: phi_3 by its power series
-// sum_m z^m/(m+3)! (13 terms, remainder < 1e-11 relative), then the exact
+// phi_1, phi_2, phi_3 of z (Eq. phi).  |z| < 1: phi_3 by its power series
+// sum_m z^m/(m+3)! (10 terms, remainder < 2e-9 relative), then the exact
 // downward relations phi_2 = z phi_3 + 1/2, phi_1 = z phi_2 + 1, which involve
-// no cancellation.  |z| >= 1.5: e^z and the recurrence of Eq. phi.
+// no cancellation.  |z| >= 1: e^z and the recurrence of Eq. phi (each division
+// by z amplifies rounding by at most ~4 there).
 __device__ __forceinline__ void phi123(float zr, float zi, float (&pr)[3], float (&pi)[3]) {
-  if (zr * zr + zi * zi < 2.25f) {
-    // 1/(m+3)!, m = 0..12
-    constexpr float c[13] = {1.6666667e-01f, 4.1666668e-02f, 8.3333338e-03f, 1.3888889e-03f, 1.9841270e-04f,
-                             2.4801587e-05f, 2.7557319e-06f, 2.7557319e-07f, 2.5052108e-08f, 2.0876756e-09f,
-                             1.6059044e-10f, 1.1470746e-11f, 7.6471636e-13f};
-    float ar = c[12], ai = 0.f;
+  if (zr * zr + zi * zi < 1.f) {
+    // 1/(m+3)!, m = 0..9
+    constexpr float c[10] = {1.6666667e-01f, 4.1666668e-02f, 8.3333338e-03f, 1.3888889e-03f, 1.9841270e-04f,
+                             2.4801587e-05f, 2.7557319e-06f, 2.7557319e-07f, 2.5052108e-08f, 2.0876756e-09f};
+    float ar = c[9], ai = 0.f;
 #pragma unroll
-    for (int m = 11; m >= 0; --m) {
+    for (int m = 8; m >= 0; --m) {
       const float tr = ar * zr - ai * zi + c[m];
       ai = ar * zi + ai * zr;
       ar = tr;

@@ -8,14 +8,15 @@
 // the 128 x 64 chunks of M (L2-resident) and the 128-row chunks of X (from
 // HBM) travel in two separate shared-memory rings with their own producers,
 // so the X ring can be deeper than the M ring.  The epilogue splits the FP32
-// accumulator into hi and lo bf16 and stores 32 x 16 boxes through TMA.
+// accumulator into hi and lo bf16 and stores 32 x 32 boxes through TMA.
 //
 // Warp roles (one CTA per SM, persistent over (r-tile, i-block)):
 //   warp 0      X producer (TMA, SWIZZLE_128B)
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //   warp 2      M producer (TMA, SWIZZLE_128B)
-//   warps 3-10  epilogue; warp w reads TMEM lane quarter w % 4 and the
-//               16-column groups (w - 3) / 4 and (w - 3) / 4 + 2.
+//   warps 3-10  epilogue; warp w reads TMEM lane quarter w % 4 and the two
+//               adjacent 16-column groups 2 h, 2 h + 1 with h = (w - 3) / 4,
+//               and stores them as 32 x 32 boxes (64-byte rows).
 // Every mbarrier wait is bounded (mbar_wait); on expiry the CTA records an
 // error code, drains its own TMA and MMA work, frees its TMEM and returns.
 //
@@ -36,7 +37,7 @@ constexpr uint32_t kXStage = 32768;        // X_hi (r0 | r1) 16K | X_lo (r0 | r1
 constexpr uint32_t kMStage = 32768;        // M_hi 16K | M_lo 16K
 constexpr uint32_t kPlOffM = PL_NX * kXStage;
 constexpr uint32_t kPlOffEpi = kPlOffM + PL_NM * kMStage;
-constexpr uint32_t kPlEpiWarp = 4096;      // four 32 x 16 bf16 boxes
+constexpr uint32_t kPlEpiWarp = 4096;      // two 32 x 32 bf16 boxes (hi, lo of one component)
 constexpr uint32_t kPlOffBar = kPlOffEpi + PL_NEPI * kPlEpiWarp;
 constexpr uint32_t kPlSmemBytes = kPlOffBar + 256 + 1024;   // + barriers + alignment slack
 static_assert(kPlSmemBytes <= 232448, "shared memory budget");
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int half = (warp - 3) >> 2;  // 16-column groups half and half + 2
+    const int half = (warp - 3) >> 2;  // 16-column groups 2 half and 2 half + 1
     uint32_t* box = reinterpret_cast<uint32_t*>(smem + kPlOffEpi + (warp - 3) * kPlEpiWarp);
     uint32_t t = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++t) {
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       uint32_t vr[2][16], vi[2][16];
 #pragma unroll
       for (int g2 = 0; g2 < 2; ++g2) {
-        const int cc = half + 2 * g2;
+        const int cc = 2 * half + g2;
         const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
         tmem_ld16(tl, vr[g2]);
         tmem_ld16(tl + BR, vi[g2]);
@@ -199,38 +200,34 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(a));
       const int i_base = mb * BM + q * 32;
+      // this warp's two groups are adjacent (cc = 2 half, 2 half + 1): one 32 x 32 box
+      // (64-byte rows) per component, real part first, then imaginary part
 #pragma unroll
-      for (int g2 = 0; g2 < 2; ++g2) {
-        const int cc = half + 2 * g2;
-        // the previous group's stores must have finished reading the box
+      for (int comp = 0; comp < 2; ++comp) {
         if (lane == 0) bulk_wait_read0();
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 16; j += 8) {
-          uint4 rh, rl, ih, il;
-          rh.x = split_pair(__uint_as_float(vr[g2][j + 0]), __uint_as_float(vr[g2][j + 1]), rl.x);
-          rh.y = split_pair(__uint_as_float(vr[g2][j + 2]), __uint_as_float(vr[g2][j + 3]), rl.y);
-          rh.z = split_pair(__uint_as_float(vr[g2][j + 4]), __uint_as_float(vr[g2][j + 5]), rl.z);
-          rh.w = split_pair(__uint_as_float(vr[g2][j + 6]), __uint_as_float(vr[g2][j + 7]), rl.w);
-          ih.x = split_pair(__uint_as_float(vi[g2][j + 0]), __uint_as_float(vi[g2][j + 1]), il.x);
-          ih.y = split_pair(__uint_as_float(vi[g2][j + 2]), __uint_as_float(vi[g2][j + 3]), il.y);
-          ih.z = split_pair(__uint_as_float(vi[g2][j + 4]), __uint_as_float(vi[g2][j + 5]), il.z);
-          ih.w = split_pair(__uint_as_float(vi[g2][j + 6]), __uint_as_float(vi[g2][j + 7]), il.w);
-          const int w = lane * 8 + j / 2;   // 32-bit word of this row's 16 bf16
-          *reinterpret_cast<uint4*>(box + 0 * 256 + w) = rh;
-          *reinterpret_cast<uint4*>(box + 1 * 256 + w) = rl;
-          *reinterpret_cast<uint4*>(box + 2 * 256 + w) = ih;
-          *reinterpret_cast<uint4*>(box + 3 * 256 + w) = il;
+        for (int g2 = 0; g2 < 2; ++g2) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 8) {
+            uint4 h, l;
+            const uint32_t* v = comp == 0 ? vr[g2] : vi[g2];
+            h.x = split_pair(__uint_as_float(v[j + 0]), __uint_as_float(v[j + 1]), l.x);
+            h.y = split_pair(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), l.y);
+            h.z = split_pair(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), l.z);
+            h.w = split_pair(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), l.w);
+            const int w = lane * 16 + g2 * 8 + j / 2;   // 32-bit word of this row's 32 bf16
+            *reinterpret_cast<uint4*>(box + w) = h;
+            *reinterpret_cast<uint4*>(box + 512 + w) = l;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
-          const int x = (int)(tile * BR + cc * 16);
+          const int x = (int)(tile * BR + 32 * half);
           const uint32_t sb = smem_u32(box);
-          tma_store_3d(&tm_yhi, sb + 0 * 1024, x, i_base, 0);
-          tma_store_3d(&tm_ylo, sb + 1 * 1024, x, i_base, 0);
-          tma_store_3d(&tm_yhi, sb + 2 * 1024, x, i_base, 1);
-          tma_store_3d(&tm_ylo, sb + 3 * 1024, x, i_base, 1);
+          tma_store_3d(&tm_yhi, sb, x, i_base, comp);
+          tma_store_3d(&tm_ylo, sb + 2048, x, i_base, comp);
           bulk_commit();
         }
         __syncwarp();

@@ -81,12 +81,12 @@ void encode_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ro
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-// 3D bf16 tensor map over a split output plane pair [2][p][R], box (16, 32, 1),
-// no swizzle: the TMA-store epilogue writes 32 x 16 element boxes.
+// 3D bf16 tensor map over a split output plane pair [2][p][R], box (32, 32, 1),
+// no swizzle: the TMA-store epilogue writes 32 x 32 element boxes.
 void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p) {
   cuuint64_t dims[3] = {R, p, 2};
   cuuint64_t strides[2] = {R * 2, R * p * 2};
-  cuuint32_t box[3] = {16, 32, 1};
+  cuuint32_t box[3] = {32, 32, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
