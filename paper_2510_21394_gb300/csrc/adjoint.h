@@ -1,24 +1,32 @@
 // Discrete adjoint of the Heun-based Lawson-RK2 scheme on the device.
 //
-// Forward step (E = exp(tau K), applied in the Tucker form Q (e^{tau lam} o Q^T x)):
-//     k1 = g(t, u);  a = u + tau k1;  v = E a;  b = u + tau/2 k1;  w = E b;
-//     u' = w + tau/2 g(t + tau, v).
-// Misfit J = 1/2 sum |u(T) - u_target|^2; gradients in the real sense
-// (dJ/dRe + i dJ/dIm).  Backward step, lambda = dJ/du':
-//     mu_v  = tau/2 (D_v g)^* lambda
-//     lambda_b = E^H lambda,  lambda_a = E^H mu_v          (E^H = Q (conj(e^{tau lam}) o Q^T .))
-//     lambda_k1 = tau lambda_a + tau/2 lambda_b
-//     lambda <- lambda_a + lambda_b + (D_u g)^* lambda_k1,
+// The scheme is run in spectral form with the spectral state U^ = Q^T u as
+// the primary variable (Q = Q_d (x) ... (x) Q_1, fwd = Q^T ., bwd = Q .;
+// E = e^{tau K} acts on U^ as the diagonal e^{tau Lam}):
+//     u = bwd(U^);  k1 = g(t, u);  K^ = fwd(k1);
+//     V^ = E(U^ + tau K^);  W^ = E(U^ + tau/2 K^);  v = bwd(V^);
+//     U^' = W^ + tau/2 fwd(g(t + tau, v)),
+// which is the physical step (k1 = g(t, u); v = E(u + tau k1);
+// u' = E(u + tau/2 k1) + tau/2 g(t + tau, v)) written in the eigenbasis.
+// The first forward (U^_0 = fwd(u_0)) and the last backward (u_N = bwd(U^_N))
+// operators use the engine's precise transform; the per-step ones may be
+// reduced precision, whose error then enters only through tau-small terms.
+// Misfit J = 1/2 sum |u_N - u_target|^2; gradients in the real sense
+// (dJ/dRe + i dJ/dIm).  Spectral adjoint m^ = dJ/dU^; backward step:
+//     m_v  = (D_v g)^* (tau/2 bwd(m^'))              (physical)
+//     m^_V = fwd(m_v);  a = E^H m^_V;  b = E^H m^'   (E^H = conj(e^{tau Lam}))
+//     m^   = a + b + fwd((D_u g)^* bwd(tau a + tau/2 b)),
 // with (D_z g)^* w = conj(alpha) w + beta conj(w), alpha = gamma - 2(kappa+i zeta)|z|^2,
 // beta = -(kappa + i zeta) z^2.  Parameter gradients:
-//     dJ/dgamma, dkappa, dzeta: Re<lambda_k1, dg/dp(u)> + Re<tau/2 lambda, dg/dp(v)>,
+//     dJ/dgamma, dkappa, dzeta: Re<bwd(tau a + tau/2 b), dg/dp(u)> + Re<tau/2 bwd(m^'), dg/dp(v)>,
 //         dg/dgamma = z, dg/dkappa = -|z|^2 z, dg/dzeta = -i |z|^2 z;
-//     dJ/dnu = tau Re Z, dJ/deta = -tau Im Z,  Z = sum_steps sum conj(Q^T lambda) Lam_D (Q^T w)
-//         + conj(Q^T mu_v) Lam_D (Q^T v),  Lam_D the eigenvalues of K_D = (+)_mu D_mu,
+//     dJ/dnu = tau Re Z, dJ/deta = -tau Im Z,  Z = sum_steps sum conj(m^') Lam_D W^ + conj(m^_V) Lam_D V^,
+//         Lam_D the eigenvalues of K_D = (+)_mu D_mu,
 //     because dE/dnu = tau K_D E and dE/deta = i tau K_D E.
-// Memory: states are checkpointed every C steps in the forward sweep; each
-// segment is recomputed forward (storing u_n, v_n, Q^T v_n, Q^T w_n) and then
-// swept backward, so the cost is about three forward integrations.
+// dJ/du_0 = bwd(m^_0).  Memory: U^ is checkpointed every C steps in the
+// forward sweep; each segment is recomputed forward (storing u_n, v_n, V^_n,
+// W^_n) and then swept backward, so the cost is about three forward
+// integrations.
 #pragma once
 
 #include <cmath>
@@ -62,7 +70,8 @@ void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* 
 
 // Driver.  Eng provides: Shape shape(); cudaStream_t stream(); long long& nlaunch();
 // GParams gparams(); LamVecs lamvecs(); T* alloc(size_t n) (freed by the caller afterwards);
-// void tuckerT(const T* X, T* Y, bool fwd) on planar tensors (X, Y distinct).
+// void tuckerT(const T* X, T* Y, bool fwd) and tuckerT_precise(...) on planar
+// tensors (X, Y distinct).
 template <typename T, class Eng>
 void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, const T* target, int C, T* grad_u0,
                         double* grad_params, double* loss) {
@@ -85,71 +94,73 @@ void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, 
     svh[k] = buf(T2);
     swh[k] = buf(T2);
   }
+  T* uh = buf(T2);   // U^ (forward sweep)
   T* u = buf(T2);
-  T* a = buf(T2);
-  T* b = buf(T2);
   T* x1 = buf(T2);
   T* x2 = buf(T2);
-  T* lam = buf(T2);
-  T* mu = buf(T2);
-  T* la = buf(T2);
-  T* lb = buf(T2);
+  T* a = buf(T2);
+  T* b = buf(T2);
+  T* mh = buf(T2);   // m^
+  T* mv = buf(T2);
+  T* y = buf(T2);
   double* acc = reinterpret_cast<double*>(buf((ADJ_NACC * sizeof(double) + sizeof(T) - 1) / sizeof(T)));
   FCGLE_CUDA(cudaMemsetAsync(acc, 0, ADJ_NACC * sizeof(double), st));
-
-  // one forward step u -> u (Tucker-form exp), optionally storing u_n, v, Q^T v, Q^T w
-  auto fstep = [&](double t, T* uu, T* keep_u, T* keep_v, T* keep_vh, T* keep_wh) {
-    if (keep_u) FCGLE_CUDA(cudaMemcpyAsync(keep_u, uu, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    // a = u + tau g(t, u), b = u + tau/2 g(t, u)
-    gcombo<T>(s, gp0, t, uu, nullptr, nullptr, 1, 0, 1, 0, tau, 0, a, st, nl);
-    gcombo<T>(s, gp0, t, uu, nullptr, nullptr, 1, 0, 1, 0, 0.5 * tau, 0, b, st, nl);
-    // v = E a
-    e.tuckerT(a, x1, true);
-    adj_scale_exp<T>(s, lv, tau, false, x1, x2, st, nl);
-    if (keep_vh) FCGLE_CUDA(cudaMemcpyAsync(keep_vh, x2, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    T* v = keep_v ? keep_v : a;
-    e.tuckerT(x2, v, false);
-    // w = E b
-    e.tuckerT(b, x1, true);
-    adj_scale_exp<T>(s, lv, tau, false, x1, x2, st, nl);
-    if (keep_wh) FCGLE_CUDA(cudaMemcpyAsync(keep_wh, x2, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    e.tuckerT(x2, b, false);
-    // u' = w + tau/2 g(t + tau, v)
-    gcombo<T>(s, gp0, t + tau, v, b, nullptr, 1, 0, 0, 1, 0.5 * tau, 0, uu, st, nl);
+  auto copy = [&](T* dst, const T* src) {
+    FCGLE_CUDA(cudaMemcpyAsync(dst, src, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
   };
 
-  // ---- forward sweep with checkpoints
-  FCGLE_CUDA(cudaMemcpyAsync(u, u0, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  // one forward step on the spectral state uh, optionally keeping u_n, v_n, V^_n, W^_n
+  auto fstep = [&](double t, T* keep_u, T* keep_v, T* keep_vh, T* keep_wh) {
+    T* uu = keep_u ? keep_u : u;
+    e.tuckerT(uh, uu, false);                                                    // u = bwd(U^)
+    gcombo<T>(s, gp0, t, uu, nullptr, nullptr, 1, 0, 0, 0, 1, 0, x1, st, nl);   // k1 = g(t, u)
+    e.tuckerT(x1, x2, true);                                                     // K^
+    T* vh = keep_vh ? keep_vh : a;
+    T* wh = keep_wh ? keep_wh : b;
+    adj_axpby<T>(s, 1.0, uh, tau, x2, x1, st, nl);
+    adj_scale_exp<T>(s, lv, tau, false, x1, vh, st, nl);                         // V^ = E(U^ + tau K^)
+    adj_axpby<T>(s, 1.0, uh, 0.5 * tau, x2, x1, st, nl);
+    adj_scale_exp<T>(s, lv, tau, false, x1, wh, st, nl);                         // W^ = E(U^ + tau/2 K^)
+    T* v = keep_v ? keep_v : x1;
+    e.tuckerT(vh, v, false);                                                     // v = bwd(V^)
+    gcombo<T>(s, gp0, t + tau, v, nullptr, nullptr, 1, 0, 0, 0, 1, 0, y, st, nl);   // g(t + tau, v)
+    e.tuckerT(y, x2, true);
+    adj_axpby<T>(s, 1.0, wh, 0.5 * tau, x2, uh, st, nl);                         // U^' = W^ + tau/2 fwd(g)
+  };
+
+  // ---- forward sweep with checkpoints of U^
+  e.tuckerT_precise(u0, uh, true);
   for (int n = 0; n < nsteps; ++n) {
-    if (n % C == 0) FCGLE_CUDA(cudaMemcpyAsync(ck[n / C], u, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    fstep(t0 + n * tau, u, nullptr, nullptr, nullptr, nullptr);
+    if (n % C == 0) copy(ck[n / C], uh);
+    fstep(t0 + n * tau, nullptr, nullptr, nullptr, nullptr);
   }
-  adj_misfit<T>(s, u, target, lam, acc, st, nl);
+  e.tuckerT_precise(uh, u, false);                 // u_N
+  adj_misfit<T>(s, u, target, x1, acc, st, nl);    // x1 = u_N - target, loss
+  e.tuckerT_precise(x1, mh, true);                 // m^_N
 
   // ---- backward sweep, segment by segment
   for (int k = nseg - 1; k >= 0; --k) {
     const int n0 = k * C, n1 = std::min(nsteps, n0 + C);
-    FCGLE_CUDA(cudaMemcpyAsync(u, ck[k], T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    for (int n = n0; n < n1; ++n) fstep(t0 + n * tau, u, su[n - n0], sv[n - n0], svh[n - n0], swh[n - n0]);
+    copy(uh, ck[k]);
+    for (int n = n0; n < n1; ++n) fstep(t0 + n * tau, su[n - n0], sv[n - n0], svh[n - n0], swh[n - n0]);
     for (int n = n1 - 1; n >= n0; --n) {
       const int j = n - n0;
-      // mu_v = tau/2 (D_v g)^* lambda
-      adj_gv<T>(s, gp0, sv[j], lam, 0.5 * tau, mu, acc, st, nl);
-      // lambda_b = E^H lambda;  Z += conj(Q^T lambda) Lam_D (Q^T w)
-      e.tuckerT(lam, x1, true);
-      adj_spec_dot<T>(s, lv, x1, swh[j], acc, st, nl);
-      adj_scale_exp<T>(s, lv, tau, true, x1, x2, st, nl);
-      e.tuckerT(x2, lb, false);
-      // lambda_a = E^H mu_v;  Z += conj(Q^T mu_v) Lam_D (Q^T v)
-      e.tuckerT(mu, x1, true);
-      adj_spec_dot<T>(s, lv, x1, svh[j], acc, st, nl);
-      adj_scale_exp<T>(s, lv, tau, true, x1, x2, st, nl);
-      e.tuckerT(x2, la, false);
-      // lambda <- lambda_a + lambda_b + (D_u g)^* (tau lambda_a + tau/2 lambda_b)
-      adj_gu<T>(s, gp0, su[j], la, lb, tau, 0.5 * tau, lam, acc, st, nl);
+      adj_spec_dot<T>(s, lv, mh, swh[j], acc, st, nl);        // Z += conj(m^') Lam_D W^
+      e.tuckerT(mh, y, false);                                 // bwd(m^')
+      adj_gv<T>(s, gp0, sv[j], y, 0.5 * tau, mv, acc, st, nl);  // m_v = (D_v g)^* (tau/2 bwd(m^'))
+      e.tuckerT(mv, x1, true);                                 // m^_V
+      adj_spec_dot<T>(s, lv, x1, svh[j], acc, st, nl);        // Z += conj(m^_V) Lam_D V^
+      adj_scale_exp<T>(s, lv, tau, true, x1, a, st, nl);      // a = E^H m^_V
+      adj_scale_exp<T>(s, lv, tau, true, mh, b, st, nl);      // b = E^H m^'
+      adj_axpby<T>(s, tau, a, 0.5 * tau, b, x1, st, nl);      // tau a + tau/2 b
+      e.tuckerT(x1, y, false);
+      adj_gv<T>(s, gp0, su[j], y, 1.0, mv, acc, st, nl);      // (D_u g)^* bwd(tau a + tau/2 b)
+      e.tuckerT(mv, x2, true);
+      adj_axpby<T>(s, 1.0, a, 1.0, b, x1, st, nl);
+      adj_axpby<T>(s, 1.0, x1, 1.0, x2, mh, st, nl);          // m^ = a + b + fwd(...)
     }
   }
-  FCGLE_CUDA(cudaMemcpyAsync(grad_u0, lam, T2 * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  e.tuckerT_precise(mh, grad_u0, false);            // dJ/du_0 = bwd(m^_0)
   double h[ADJ_NACC];
   FCGLE_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
   FCGLE_CUDA(cudaStreamSynchronize(st));

@@ -279,6 +279,7 @@ class Engine : public EngineBase {
   }
   void release_all() { adj_mem_.clear(); }
   void tuckerT(const T* X, T* Y, bool fwd) { tucker(X, Y, fwd); }
+  void tuckerT_precise(const T* X, T* Y, bool fwd) { tucker(X, Y, fwd); }
 
   void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
                void* grad_u0, double* grad_params, double* loss) override {

@@ -385,6 +385,7 @@ class EngineB3 : public EngineBase {
     FCGLE_LAUNCHED(launches);
     tucker(V, fwd, b3::EpiStoreF32{P32(), Y});
   }
+  void tuckerT_precise(const float* X, float* Y, bool fwd) { tucker_f32(X, Y, fwd); }
 
   void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
                void* grad_u0, double* grad_params, double* loss) override {

@@ -39,7 +39,9 @@ def _dev(x, dt):
     return torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x3", 2e-3)])
+# split-BF16: the adjoint runs in the eigenbasis with FP32 first / last
+# transforms, so the reduced-precision error enters through tau-small terms only
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x3", 2e-4)])
 @pytest.mark.parametrize("ckpt", [0, 1, 4])
 def test_gradient_matches_oracle(fc, prec, tol, ckpt):
     P, S, g, u0, target, src = _case()

@@ -54,11 +54,14 @@ def test_config5_gradients(fc):
                                     ckpt_every=CK)
     rel_u = float(torch.linalg.vector_norm(g32.to(torch.complex128) - g64) / torch.linalg.vector_norm(g64))
     rel_p = float(np.max(np.abs(np.array(gp32) - np.array(gp64)) / np.abs(np.array(gp64))))
-    print(f"config5: J = {loss:.6e}; bf16x3 vs fp64: grad_u0 rel {rel_u:.2e}, params max rel {rel_p:.2e}")
-    # J compares two nearby states (target: parameters x 1.05), so the ~1e-5
-    # relative error of the split-BF16 forward map becomes ~1e-3 of J and a
-    # few 1e-2 of grad J; measured on GB300: 2e-3, 1.8e-2, 6.7e-3.
-    assert loss32 == pytest.approx(loss, rel=5e-3)
-    assert rel_u < 5e-2 and rel_p < 2e-2
+    rel_j = abs(loss32 - loss) / loss
+    print(f"config5: J = {loss:.6e}; bf16x3 vs fp64: J rel {rel_j:.2e}, grad_u0 rel {rel_u:.2e}, "
+          f"params max rel {rel_p:.2e}")
+    # J compares two nearby states (target: parameters x 1.05), so relative
+    # errors of the forward map are amplified in J and grad J; the split-BF16
+    # adjoint runs in the eigenbasis with FP32 first / last transforms.
+    # Measured on GB300: grad_u0 5.5e-5, parameters 9.3e-6.
+    assert rel_j < 1e-4
+    assert rel_u < 5e-4 and rel_p < 1e-4
     s64.close()
     s32.close()
