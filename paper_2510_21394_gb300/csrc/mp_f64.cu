@@ -113,10 +113,98 @@ void mp_f64(const double* X, double* Y, const double* M, int p, size_t R, bool c
   FCGLE_LAUNCHED(nl);
 }
 
+// FP32 REAL mode with larger register tiles: 128 x 128 block tile, 8 x 8
+// outputs per thread, K in steps of 8 through double-buffered shared memory.
+// Needs p % 8 == 0 and R % 8 == 0 (then a thread's 8 rows never straddle the
+// re/im plane boundary and its stores are 16-byte vectors).
+constexpr int FM = 128, FN = 128, FK = 8, FT = 256;
+
+__global__ void __launch_bounds__(FT) mp_f32_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                                    const float* __restrict__ B, int p, long long R) {
+  __shared__ __align__(16) float As[2][FK][FM];
+  __shared__ __align__(16) float Bs[2][FK][FN];
+  const long long rows = 2 * R;
+  const long long Rp = R * (long long)p;
+  const long long row0 = (long long)blockIdx.x * FM;
+  const int col0 = blockIdx.y * FN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;   // cols tx*8.., rows ty*8..
+  const int lrow = tid >> 1, lk = (tid & 1) * 4;   // loader: one float4 of A and one of B
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  auto load = [&](int k0, float4& a, float4& b) {
+    const long long row = row0 + lrow;
+    const int col = col0 + lrow;
+    a = row < rows ? *reinterpret_cast<const float4*>(X + row * p + k0 + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
+    b = col < p ? *reinterpret_cast<const float4*>(B + (long long)col * p + k0 + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto stash = [&](int buf, const float4& a, const float4& b) {
+    As[buf][lk + 0][lrow] = a.x;
+    As[buf][lk + 1][lrow] = a.y;
+    As[buf][lk + 2][lrow] = a.z;
+    As[buf][lk + 3][lrow] = a.w;
+    Bs[buf][lk + 0][lrow] = b.x;
+    Bs[buf][lk + 1][lrow] = b.y;
+    Bs[buf][lk + 2][lrow] = b.z;
+    Bs[buf][lk + 3][lrow] = b.w;
+  };
+  float4 ra, rb;
+  load(0, ra, rb);
+  stash(0, ra, rb);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < p; k0 += FK) {
+    const bool more = k0 + FK < p;
+    if (more) load(k0 + FK, ra, rb);
+#pragma unroll
+    for (int k = 0; k < FK; ++k) {
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8 + 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      stash(buf ^ 1, ra, rb);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+  const long long r0 = row0 + ty * 8;
+  if (r0 >= rows) return;
+  const long long c = r0 >= R ? 1 : 0;
+  const long long rr = r0 - c * R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = col0 + tx * 8 + j;
+    if (col >= p) continue;
+    float* dst = Y + c * Rp + (long long)col * R + rr;
+    *reinterpret_cast<float4*>(dst) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+  }
+}
+
 void mp_f32(const float* X, float* Y, const float* M, int p, size_t R, cudaStream_t st, long long& nl) {
   const long long rows = 2 * (long long)R;
-  dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)((p + BN - 1) / BN));
-  mp_simt_kernel<float, false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+  if (p % 8 == 0 && R % 8 == 0) {
+    dim3 grid((unsigned)((rows + FM - 1) / FM), (unsigned)((p + FN - 1) / FN));
+    mp_f32_kernel<<<grid, FT, 0, st>>>(X, Y, M, p, (long long)R);
+  } else {
+    dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)((p + BN - 1) / BN));
+    mp_simt_kernel<float, false><<<grid, NT, 0, st>>>(X, Y, M, p, (long long)R);
+  }
   FCGLE_LAUNCHED(nl);
 }
 
