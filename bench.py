@@ -38,14 +38,19 @@ METRIC = "DoF*steps/s"
 UNIT = "DoF*steps/s"
 
 
-def workload_config(n, precision="bf16x3"):
+SCHEME_NAMES = {"krogstad": "Krogstad exponential RK4 (phi_1..phi_3)", "etd2rk": "ETD2RK", "lie": "linearly-implicit Euler",
+                "lbdf2": "linearised BDF2", "strang": "Strang splitting", "lawson_euler": "Lawson-Euler",
+                "lawson_rk2": "Lawson-RK2"}
+
+
+def workload_config(n, precision="bf16x3", scheme="krogstad", tau=TAU):
     return {
         "workload": f"3D FCGLE {n}^3 on (-10,10)^3, alpha=(1.2,1.5,1.8), nu=1, eta=0.5, gamma=1, kappa=1, "
-                    f"zeta=0.5; Krogstad exponential RK4 (phi_1..phi_3), tau=1e-3; u0 = Gaussian bump x "
+                    f"zeta=0.5; {SCHEME_NAMES[scheme]}, tau={tau:g}; u0 = Gaussian bump x "
                     f"smoothed random phase (seed 1)",
         "grid": [n, n, n],
-        "scheme": "krogstad",
-        "tau": TAU,
+        "scheme": scheme,
+        "tau": tau,
         "precision": precision,
         "storage": "complex64" if precision == "bf16x3" else "complex128",
         "l2": "inputs larger than L2 (each 256^3 tensor is 134 MB complex64)",
@@ -286,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty_like(u0)
 
     # warm-up (also fills the cached phi tensors)
-    solver.integrate("krogstad", TAU, args.warmup, u0, out=out)
+    solver.integrate(args.scheme, args.tau, args.warmup, u0, out=out)
     solver.sync()
     torch.cuda.synchronize()
 
@@ -299,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    solver.integrate("krogstad", TAU, args.steps, u0, out=out)
+    solver.integrate(args.scheme, args.tau, args.steps, u0, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -342,17 +347,19 @@ def run_ours(args, rank, world, local_rank):
     # the whole step against HBM: algorithmic bytes per element of one Krogstad step
     # (16 plain products x 16 B; EpiFhat 32, 3 x EpiStageD 24, EpiKrog2 32, EpiKrog3 40,
     # EpiKrogFinal 40, EpiUpdateG 24) over the padded tensor
-    step_bytes = KROGSTAD_BYTES_PER_ELEM * P
-    step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
-    step_roof = {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
-                 "frac": round(step_gbs / peak, 4), "floor_ms": round(step_bytes / (peak * 1e9) * 1e3, 4)}
+    step_roof = None
+    if args.scheme == "krogstad":
+        step_bytes = KROGSTAD_BYTES_PER_ELEM * P
+        step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
+        step_roof = {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_gbs / peak, 4), "floor_ms": round(step_bytes / (peak * 1e9) * 1e3, 4)}
 
     # ---- end to end through the C ABI with host buffers
     hin = torch.from_numpy(u0_np.astype(np.complex64)).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    solver.integrate_host("krogstad", TAU, args.steps, hin, hout)
+    solver.integrate_host(args.scheme, args.tau, args.steps, hin, hout)
     e2e_s = max_over_ranks(time.perf_counter() - t1, world)
     e2e = {"value": aggregate_rate(dof, args.steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": hin.numel() * 8 / args.steps, "d2h_bytes_per_step": hout.numel() * 8 / args.steps,
@@ -366,17 +373,17 @@ def run_ours(args, rank, world, local_rank):
         s64 = fcgle.Solver(ns, BOXES, ALPHAS, **PARS, precision="fp64")
         v64 = torch.from_numpy(u0_np).cuda()
         o64 = torch.empty_like(v64)
-        s64.integrate("krogstad", TAU, 1, v64, out=o64)
+        s64.integrate(args.scheme, args.tau, 1, v64, out=o64)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        s64.integrate("krogstad", TAU, 2, v64, out=o64)
+        s64.integrate(args.scheme, args.tau, 2, v64, out=o64)
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1) / 2
-        s64.integrate("krogstad", TAU, acc_steps, v64, out=o64)
-        solver.integrate("krogstad", TAU, acc_steps, u0, out=out)
+        s64.integrate(args.scheme, args.tau, acc_steps, v64, out=o64)
+        solver.integrate(args.scheme, args.tau, acc_steps, u0, out=out)
         torch.cuda.synchronize()
         err = float(torch.linalg.vector_norm(out.to(torch.complex128) - o64) / torch.linalg.vector_norm(o64))
         s64.sync()
@@ -388,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
     solver.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.scheme == "krogstad":
         try:
             res = run_cpu_sample_subprocess(n, 1, 0.0, timeout_s=900)
             cpu = {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
@@ -400,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n),
+                "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n, "bf16x3", args.scheme, args.tau),
                 "roofline": roofline, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "setup_s": round(setup_s, 3)}
         line.update(extra)
@@ -508,6 +515,71 @@ def run_batched(args, rank, world, local_rank):
     return 0
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """Gradient of J = 1/2 ||u(T) - u_target||^2 w.r.t. u0 and (nu, eta, gamma, kappa, zeta):
+    3D 128^3, alpha = 1.5, Lawson-RK2, tau = 2e-3, 250 steps, checkpoints every 25,
+    u_target from a forward run with the parameters scaled by 1.05."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        import __graft_entry__ as g
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2510_21394_gb300 import fcgle, inputs
+    ns, boxes, al = [128] * 3, [(-10.0, 10.0)] * 3, [1.5] * 3
+    pars = [1.0, 0.5, 1.0, 1.0, 0.5]
+    tau, m, ck = 2e-3, 250, 25
+    u0n = inputs.gaussian_random_phase(ns, boxes, seed=3)
+    out = {}
+    stream = torch.cuda.current_stream()
+    s64 = fcgle.Solver(ns, boxes, al, *pars, precision="fp64")
+    v64 = torch.from_numpy(u0n).cuda()
+    s64.set_coefficients(*[1.05 * x for x in pars])
+    target = s64.integrate("lawson_rk2", tau, m, v64)
+    s64.set_coefficients(*pars)
+    for prec in ("bf16x3", "fp64"):
+        s = s64 if prec == "fp64" else fcgle.Solver(ns, boxes, al, *pars, precision=prec)
+        dt = torch.complex128 if prec == "fp64" else torch.complex64
+        v, tg = v64.to(dt), target.to(dt)
+        s.adjoint("lawson_rk2", tau, 5, v, tg, ckpt_every=5)   # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss, gu, gp = s.adjoint("lawson_rk2", tau, m, v, tg, ckpt_every=ck)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        out[prec] = dict(seconds=sec, loss=loss, gu=gu.to(torch.complex128), gp=gp)
+        if prec != "fp64":
+            s.close()
+    dof = 128 ** 3
+    g64 = out["fp64"]["gu"]
+    o = out["bf16x3"]
+    acc = {"loss_rel": abs(o["loss"] - out["fp64"]["loss"]) / out["fp64"]["loss"],
+           "grad_u0_rel": float(torch.linalg.vector_norm(o["gu"] - g64) / torch.linalg.vector_norm(g64)),
+           "params_max_rel": float(max(abs(a - b) / abs(b) for a, b in zip(o["gp"], out["fp64"]["gp"])))}
+    s64.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": aggregate_rate(dof, m, o["seconds"], world), "unit": UNIT,
+                "n_gpus": world, "steps": m, "warmup": 1, "ms_per_step": 1e3 * o["seconds"] / m,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+                "data": "synthetic",
+                "config": {"workload": "adjoint: 3D 128^3 on (-10,10)^3, alpha=1.5, nu=1, eta=0.5, gamma=1, kappa=1, "
+                                       "zeta=0.5, Lawson-RK2, tau=2e-3, 250 steps, checkpoints every 25; target from "
+                                       "parameters x 1.05; gradient w.r.t. u0 and (nu, eta, gamma, kappa, zeta)",
+                           "note": "value = grid points x steps of the forward map per second of one gradient "
+                                   "(forward sweep, recompute and backward sweep)",
+                           "parallelism": "replicas (one independent gradient per GPU)"},
+                "fp64_gpu": {"value": aggregate_rate(dof, m, out["fp64"]["seconds"], world),
+                             "seconds": out["fp64"]["seconds"]},
+                "seconds": o["seconds"], "accuracy_vs_fp64_gpu": acc}
+        print(json.dumps(line))
+    return 0
+
+
 def run_mp_only(args):
     """Raw mode products on internal-layout buffers, for kernel profiling."""
     import torch
@@ -549,8 +621,12 @@ def main():
     ap.add_argument("--mp-only", type=int, default=0, metavar="REPS",
                     help="only run REPS x 3 raw mode products (all directions) of the n^3 workload (profiling)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
-    ap.add_argument("--workload", default="cube", choices=["cube", "batched"],
-                    help="cube: one 3D n^3 Krogstad instance (default); batched: 96 uneven ETD2RK instances")
+    ap.add_argument("--scheme", default="krogstad", choices=sorted(SCHEME_NAMES),
+                    help="cube workload: time-stepping scheme (default krogstad, the benchmark)")
+    ap.add_argument("--tau", type=float, default=TAU)
+    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "adjoint"],
+                    help="cube: one 3D n^3 instance (default Krogstad); batched: 96 uneven ETD2RK instances; "
+                         "adjoint: gradient of a final-time misfit, 128^3 Lawson-RK2")
     args = ap.parse_args()
     if args.mp_only:
         return run_mp_only(args)
@@ -576,6 +652,8 @@ def main():
     try:
         if args.workload == "batched":
             return run_batched(args, rank, world, local_rank)
+        if args.workload == "adjoint":
+            return run_adjoint(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
