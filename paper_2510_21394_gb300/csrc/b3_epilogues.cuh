@@ -200,6 +200,50 @@ __device__ __forceinline__ void phi123(float zr, float zi, float (&pr)[3], float
   }
 }
 
+// phi_1..phi_3 along the ray of one launch: z = w s with w = theta (nu + i eta)
+// fixed and s the real eigenvalue sum of the element, so the series of phi_3
+// becomes a polynomial in the real s with complex coefficients
+// c_m = w^m / (m+3)! (computed on the host in FP64) and each Horner step costs
+// two FMAs instead of a complex multiply-add.  |z| >= 1 (|s| >= smax) takes
+// the recurrence branch of phi123.
+struct PhiPoly {
+  float cr[10] = {0}, ci[10] = {0};
+  float smax = 0.f;
+  float wr = 0.f, wi = 0.f;
+};
+__device__ __forceinline__ void phi123_s(const PhiPoly& P, float s, float (&pr)[3], float (&pi)[3]) {
+  const float zr = P.wr * s, zi = P.wi * s;
+  if (fabsf(s) < P.smax) {
+    float ar = P.cr[9], ai = P.ci[9];
+#pragma unroll
+    for (int m = 8; m >= 0; --m) {
+      ar = fmaf(ar, s, P.cr[m]);
+      ai = fmaf(ai, s, P.ci[m]);
+    }
+    pr[2] = ar;
+    pi[2] = ai;
+    pr[1] = zr * ar - zi * ai + 0.5f;
+    pi[1] = zr * ai + zi * ar;
+    pr[0] = zr * pr[1] - zi * pi[1] + 1.f;
+    pi[0] = zr * pi[1] + zi * pr[1];
+  } else {
+    phi123(zr, zi, pr, pi);
+  }
+}
+
+// real eigenvalue sums s (lam = (nu + i eta) s) at the elements of lam_eval
+template <int V>
+__device__ __forceinline__ void lam_sum(const LamF& L, int i, uint32_t r, float (&sv)[V]) {
+  float base = L.lam[L.d - 1][i];
+  uint32_t j1 = r;
+  if (L.d >= 2) {
+    j1 = r % (uint32_t)L.p[0];
+    if (L.d == 3) base += L.lam[1][r / (uint32_t)L.p[0]];
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) sv[v] = L.d >= 2 ? base + L.lam[0][j1 + v] : base;
+}
+
 // phi_k(z), any k >= 1: Horner form of the series
 // (1/k!)(1 + z/(k+1)(1 + z/(k+2)(...))) for |z| < 1.5, recurrence otherwise.
 __device__ __forceinline__ void phik(int k, float zr, float zi, float& fr, float& fi) {
@@ -404,6 +448,7 @@ struct EpiFhat {
   float c;
   int update_uh;
   SplitOut S;
+  PhiPoly ph;   // phi series coefficients of this launch (theta = theta)
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
     ldv<V>(Uh + q, in[0]);
@@ -413,14 +458,20 @@ struct EpiFhat {
   __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
                         const float (&in)[2][V]) const {
     float lr[V], li[V], fr[V], fi[V], sr[V], si[V];
-    lam_eval<V>(L, i, r, lr, li);
+    float sv[V];
+    lam_sum<V>(L, i, r, sv);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      lr[v] = L.c_re * sv[v];
+      li[v] = L.c_im * sv[v];
+    }
     cmulv<V>(lr, li, in[0], in[1], fr, fi);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       fr[v] += re[v];
       fi[v] += im[v];
       float pr[3], pi[3];
-      phi123(theta * lr[v], theta * li[v], pr, pi);
+      phi123_s(ph, sv[v], pr, pi);
       sr[v] = c * (pr[0] * fr[v] - pi[0] * fi[v]);
       si[v] = c * (pr[0] * fi[v] + pi[0] * fr[v]);
     }
@@ -449,6 +500,7 @@ struct EpiKrog2 {
   float* D2;
   float tau;
   SplitOut S;
+  PhiPoly ph;   // phi series coefficients of this launch (theta = tau / 2)
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
     ldv_ro<V>(Fh + q, in[0]);
@@ -459,13 +511,13 @@ struct EpiKrog2 {
                         const float (&in)[2][V]) const {
     stv<V>(D2 + q, re);
     stv<V>(D2 + P + q, im);
-    float lr[V], li[V], sr[V], si[V];
-    lam_eval<V>(L, i, r, lr, li);
-    const float th = 0.5f * tau;
+    float sr[V], si[V];
+    float sv[V];
+    lam_sum<V>(L, i, r, sv);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float pr[3], pi[3];
-      phi123(th * lr[v], th * li[v], pr, pi);
+      phi123_s(ph, sv[v], pr, pi);
       const float ar = 0.5f * (pr[0] * in[0][v] - pi[0] * in[1][v]) + (pr[1] * re[v] - pi[1] * im[v]);
       const float ai = 0.5f * (pr[0] * in[1][v] + pi[0] * in[0][v]) + (pr[1] * im[v] + pi[1] * re[v]);
       sr[v] = tau * ar;
@@ -489,6 +541,7 @@ struct EpiKrog3 {
   float* W;
   float tau;
   SplitOut S;
+  PhiPoly ph;   // phi series coefficients of this launch (theta = tau)
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
     ldv_ro<V>(Fh + q, in[0]);
@@ -499,12 +552,13 @@ struct EpiKrog3 {
   template <int V>
   __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
                         const float (&in)[4][V]) const {
-    float lr[V], li[V], sr[V], si[V], wr[V], wi[V];
-    lam_eval<V>(L, i, r, lr, li);
+    float sr[V], si[V], wr[V], wi[V];
+    float sv[V];
+    lam_sum<V>(L, i, r, sv);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float pr[3], pi[3];
-      phi123(tau * lr[v], tau * li[v], pr, pi);
+      phi123_s(ph, sv[v], pr, pi);
       const float fr = pr[0] * in[0][v] - pi[0] * in[1][v], fi = pr[0] * in[1][v] + pi[0] * in[0][v];
       sr[v] = tau * (fr + 2.f * (pr[1] * re[v] - pi[1] * im[v]));
       si[v] = tau * (fi + 2.f * (pr[1] * im[v] + pi[1] * re[v]));
@@ -530,6 +584,7 @@ struct EpiKrogFinal {
   float* Uh;
   float tau;
   SplitOut S;
+  PhiPoly ph;   // phi series coefficients of this launch (theta = tau)
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[4][V]) const {
     ldv_ro<V>(W + q, in[0]);
@@ -540,12 +595,13 @@ struct EpiKrogFinal {
   template <int V>
   __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
                         const float (&in)[4][V]) const {
-    float lr[V], li[V], sr[V], si[V], ur[V], ui[V];
-    lam_eval<V>(L, i, r, lr, li);
+    float sr[V], si[V], ur[V], ui[V];
+    float sv[V];
+    lam_sum<V>(L, i, r, sv);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float pr[3], pi[3];
-      phi123(tau * lr[v], tau * li[v], pr, pi);
+      phi123_s(ph, sv[v], pr, pi);
       const float cr = tau * (4.f * pr[2] - pr[1]), ci = tau * (4.f * pi[2] - pi[1]);
       sr[v] = in[0][v] + cr * re[v] - ci * im[v];
       si[v] = in[1][v] + cr * im[v] + ci * re[v];
@@ -568,6 +624,7 @@ struct EpiEtd2 {
   float* Uh;
   float tau;
   SplitOut S;
+  PhiPoly ph;   // phi series coefficients of this launch (theta = tau)
   template <int V>
   __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
     ldv<V>(Uh + q, in[0]);
@@ -576,12 +633,13 @@ struct EpiEtd2 {
   template <int V>
   __device__ void store(uint32_t q, int i, uint32_t r, const float (&re)[V], const float (&im)[V],
                         const float (&in)[2][V]) const {
-    float lr[V], li[V], sr[V], si[V], ur[V], ui[V];
-    lam_eval<V>(L, i, r, lr, li);
+    float sr[V], si[V], ur[V], ui[V];
+    float sv[V];
+    lam_sum<V>(L, i, r, sv);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float pr[3], pi[3];
-      phi123(tau * lr[v], tau * li[v], pr, pi);
+      phi123_s(ph, sv[v], pr, pi);
       sr[v] = tau * (pr[1] * re[v] - pi[1] * im[v]);
       si[v] = tau * (pr[1] * im[v] + pi[1] * re[v]);
       ur[v] = in[0][v] + sr[v];

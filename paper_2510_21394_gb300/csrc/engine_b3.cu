@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -584,6 +585,26 @@ class EngineB3 : public EngineBase {
     return f;
   }
 
+  // coefficients of the phi_3 series along z = theta (nu + i eta) s, s real (b3::phi123_s)
+  b3::PhiPoly phipoly(double theta) const {
+    b3::PhiPoly P;
+    const std::complex<double> w(theta * prm_.nu, theta * prm_.eta);
+    std::complex<double> wm(1.0, 0.0);
+    double fact = 6.0;   // (m + 3)! at m = 0
+    for (int m = 0; m < 10; ++m) {
+      const std::complex<double> c = wm / fact;
+      P.cr[m] = (float)c.real();
+      P.ci[m] = (float)c.imag();
+      wm *= w;
+      fact *= (double)(m + 4);
+    }
+    const double aw = std::abs(w);
+    P.smax = aw > 0.0 ? (float)(1.0 / aw) : 3.0e38f;
+    P.wr = (float)w.real();
+    P.wi = (float)w.imag();
+    return P;
+  }
+
   // spectral scalar f(theta lam), evaluated on the fly by the epilogues (b3 fspec kinds)
   static int fkind(int func, int k) {
     if (func == FCGLE_F_INV) return 0;
@@ -688,11 +709,11 @@ class EngineB3 : public EngineBase {
       case FCGLE_ETD2RK: {
         float *Uh = F32(kUh), *Fh = F32(kFh);
         // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
-        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V});
+        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V, phipoly(tau)});
         // a = u + bwd(S1);  D = g(t + tau, a) - g(t, u)
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, gtime(t + tau), gtime(t), V});
         // U^_{n+1} = a^ + tau phi_2(tau Lam) o D^
-        tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V});
+        tucker(V, true, b3::EpiEtd2{P32(), lf_, Uh, ft, V, phipoly(tau)});
         // u_{n+1} = bwd(U^_{n+1});  next G = g(t + tau, u_{n+1})
         tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 0.f, 1.f, V});
         break;
@@ -701,17 +722,17 @@ class EngineB3 : public EngineBase {
         float *Uh = F32(kUh), *Fh = F32(kFh), *D2 = F32(kD2), *Wc = F32(kD3);
         const b3::GTime tn = gtime(t), th = gtime(t + tau / 2), t1 = gtime(t + tau);
         // F^ = Lam o U^ + G^;  S = tau/2 phi_1(tau/2 Lam) F^
-        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, 0.5f * ft, 0.5f * ft, 0, V});
+        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, 0.5f * ft, 0.5f * ft, 0, V, phipoly(tau / 2)});
         // U_n2 = u + bwd(S);  D_2 = g(t + tau/2, U_n2) - g(t, u)
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
         // D^_2;  S = tau (1/2 phi_1(tau/2 Lam) F^ + phi_2(tau/2 Lam) D^_2)
-        tucker(V, true, b3::EpiKrog2{P32(), lf_, Fh, D2, ft, V});
+        tucker(V, true, b3::EpiKrog2{P32(), lf_, Fh, D2, ft, V, phipoly(tau / 2)});
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, th, tn, V});
         // D^_3;  S = tau (phi_1 F^ + 2 phi_2 D^_3);  W = part of the final combination
-        tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V});
+        tucker(V, true, b3::EpiKrog3{P32(), lf_, Fh, D2, Wc, ft, V, phipoly(tau)});
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, t1, tn, V});
         // D^_4;  U^_{n+1} = U^ + W + tau (4 phi_3 - phi_2) D^_4
-        tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V});
+        tucker(V, true, b3::EpiKrogFinal{P32(), lf_, Wc, Uh, ft, V, phipoly(tau)});
         // u_{n+1} = bwd(U^_{n+1});  next G = g(t + tau, u_{n+1})
         tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, t1, 0.f, 1.f, V});
         break;
