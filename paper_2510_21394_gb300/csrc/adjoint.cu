@@ -2,6 +2,7 @@
 // Planar internal layout (common.h); FP64 accumulation of every reduction
 // (warp shuffles, one atomic per block and slot).
 #include <cmath>
+#include <type_traits>
 
 #include "adjoint.h"
 
@@ -171,6 +172,99 @@ __global__ void axpby_kernel(size_t n, double a, const T* __restrict__ x1, doubl
     y[q] = (T)(a * (double)x1[q] + (x2 ? b * (double)x2[q] : 0.0));
 }
 
+// ---- FP32 forms (split-BF16 engine): per-element arithmetic in FP32 with
+// 32-bit indices (2 P < 2^32 there), reductions still accumulated in FP64.
+__device__ __forceinline__ bool lam_sum32(const LD& L, uint32_t q, float& s) {
+  double acc = 0.0;
+  bool valid = true;
+  uint32_t rem = q;
+  for (int mu = 0; mu < L.d; ++mu) {
+    const uint32_t p = (uint32_t)L.p[mu];
+    const uint32_t j = rem % p;
+    rem /= p;
+    valid = valid && (int)j < L.n[mu];
+    acc += L.lam[mu][j];
+  }
+  s = (float)acc;
+  return valid;
+}
+
+__device__ __forceinline__ void gadj_f(float gam, float kap, float zet, float zr, float zi, float wr, float wi,
+                                       float& orr, float& oi) {
+  const float m2 = zr * zr + zi * zi;
+  const float ar = gam - 2.f * kap * m2, ai = -2.f * zet * m2;
+  const float z2r = zr * zr - zi * zi, z2i = 2.f * zr * zi;
+  const float br = -(kap * z2r - zet * z2i), bi = -(kap * z2i + zet * z2r);
+  orr = ar * wr + ai * wi + br * wr + bi * wi;
+  oi = ar * wi - ai * wr + bi * wr - br * wi;
+}
+__device__ __forceinline__ void gpar_f(float zr, float zi, float wr, float wi, double (&v)[3]) {
+  const float m2 = zr * zr + zi * zi;
+  const float d = wr * zr + wi * zi, e = wr * (-zi) + wi * zr;
+  v[0] += (double)d;
+  v[1] += (double)(-m2 * d);
+  v[2] += (double)(-m2 * e);
+}
+
+__global__ void gv_kernel_f(uint32_t P, GP g, const float* __restrict__ z, const float* __restrict__ w, float c,
+                            float* __restrict__ mu, double* acc) {
+  double v[3] = {0.0, 0.0, 0.0};
+  const float gam = (float)g.gamma, kap = (float)g.kappa, zet = (float)g.zeta;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+    const float zr = z[q], zi = z[P + q], wr = c * w[q], wi = c * w[P + q];
+    float orr, oi;
+    gadj_f(gam, kap, zet, zr, zi, wr, wi, orr, oi);
+    mu[q] = orr;
+    mu[P + q] = oi;
+    gpar_f(zr, zi, wr, wi, v);
+  }
+  block_acc<3>(v, acc, ADJ_GAMMA);
+}
+
+// y = e^{z} x with z = (ar + i ai) s, formed as x + (e^z - 1) x where
+// e^z - 1 = expm1(Re z) cos(Im z) - 2 sin^2(Im z / 2) + i e^{Re z} sin(Im z):
+// the FP32 rounding then falls on the correction, not on a factor that the
+// sweeps apply again every step.  Padding (j >= n) gives y = 0.
+__global__ void scale_exp_kernel_f(uint32_t P, LD L, float ar, float ai, const float* __restrict__ x,
+                                   float* __restrict__ y) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+    float s;
+    const bool valid = lam_sum32(L, q, s);
+    float mr = -1.f, mi = 0.f;
+    if (valid) {
+      const float a = ar * s, b = ai * s;
+      float sn, cs, sh, ch;
+      sincosf(b, &sn, &cs);
+      sincosf(0.5f * b, &sh, &ch);
+      const float em = expm1f(a);
+      mr = em * cs - 2.f * sh * sh;
+      mi = (1.f + em) * sn;
+    }
+    const float xr = x[q], xi = x[P + q];
+    y[q] = xr + (mr * xr - mi * xi);
+    y[P + q] = xi + (mr * xi + mi * xr);
+  }
+}
+
+__global__ void spec_dot_kernel_f(uint32_t P, LD L, const float* __restrict__ x, const float* __restrict__ y,
+                                  double* acc) {
+  double v[2] = {0.0, 0.0};
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+    float s;
+    if (!lam_sum32(L, q, s)) continue;
+    const float xr = x[q], xi = x[P + q], yr = y[q], yi = y[P + q];
+    v[0] += (double)(s * (xr * yr + xi * yi));
+    v[1] += (double)(s * (xr * yi - xi * yr));
+  }
+  block_acc<2>(v, acc, ADJ_Z_RE);
+}
+
+__global__ void axpby_kernel_f(uint32_t n, float a, const float* __restrict__ x1, float b,
+                               const float* __restrict__ x2, float* __restrict__ y) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+    y[q] = x2 ? a * x1[q] + b * x2[q] : a * x1[q];
+}
+
 LD make_ld(const Shape& s, const LamVecs& lv) {
   LD L;
   for (int mu = 0; mu < kMaxDim; ++mu) {
@@ -192,7 +286,11 @@ void adj_misfit(const Shape& s, const T* u, const T* target, T* lam, double* acc
 template <typename T>
 void adj_gv(const Shape& s, const GParams& gp, const T* z, const T* w, double c, T* mu, double* acc, cudaStream_t st,
             long long& nl) {
-  gv_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, c, mu, acc);
+  if constexpr (std::is_same<T, float>::value)
+    gv_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, (float)c, mu,
+                                               acc);
+  else
+    gv_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, c, mu, acc);
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
@@ -204,19 +302,29 @@ void adj_gu(const Shape& s, const GParams& gp, const T* u, const T* la, const T*
 template <typename T>
 void adj_scale_exp(const Shape& s, const LamVecs& lv, double theta, bool conj, const T* x, T* y, cudaStream_t st,
                    long long& nl) {
-  scale_exp_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re,
-                                                      (conj ? -1.0 : 1.0) * theta * lv.c_im, x, y);
+  if constexpr (std::is_same<T, float>::value)
+    scale_exp_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
+                                                      (float)((conj ? -1.0 : 1.0) * theta * lv.c_im), x, y);
+  else
+    scale_exp_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re,
+                                                        (conj ? -1.0 : 1.0) * theta * lv.c_im, x, y);
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
 void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, double* acc, cudaStream_t st,
                   long long& nl) {
-  spec_dot_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), x, y, acc);
+  if constexpr (std::is_same<T, float>::value)
+    spec_dot_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), x, y, acc);
+  else
+    spec_dot_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), x, y, acc);
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
 void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* y, cudaStream_t st, long long& nl) {
-  axpby_kernel<T><<<grid_of(2 * s.P), 256, 0, st>>>(2 * s.P, a, x1, b, x2, y);
+  if constexpr (std::is_same<T, float>::value)
+    axpby_kernel_f<<<grid_of(2 * s.P), 256, 0, st>>>((uint32_t)(2 * s.P), (float)a, x1, (float)b, x2, y);
+  else
+    axpby_kernel<T><<<grid_of(2 * s.P), 256, 0, st>>>(2 * s.P, a, x1, b, x2, y);
   FCGLE_LAUNCHED(nl);
 }
 
