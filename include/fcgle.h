@@ -256,7 +256,17 @@ fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h);
 
 /* nsteps steps of every instance i from u0[i] into uT[i] (device tensors in
  * each instance's user layout and precision).  Asynchronous on the batch's
- * stream (the stream given at creation), joined back to it at the end. */
+ * stream (the stream given at creation), joined back to it at the end.
+ * use_graph: 0 enqueues every instance's kernels directly (one launch per mode
+ * product); 1 captures one step of all instances into a CUDA graph and replays
+ * it; 2 (grouped) additionally merges the instances: each phase of a step
+ * (the k-th mode product of a Tucker operator of every instance) becomes one
+ * persistent launch over a device table of all instances' tensor maps, sizes
+ * and epilogue parameters, so a step of the batch is a few launches whatever
+ * the number of instances; the phases are captured into a graph per
+ * (scheme, tau).  Grouped needs BF16X3 instances with d >= 2 and falls back to
+ * 1 otherwise; a device-side timeout inside a grouped launch is reported on
+ * instance 0's handle.  Steps with a source term run with direct launches. */
 fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,
                                    const void* const* u0, void* const* uT, int use_graph);
 

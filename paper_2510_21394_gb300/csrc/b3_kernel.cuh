@@ -177,14 +177,36 @@ __device__ __forceinline__ uint32_t split_pair(float a, float b, uint32_t& lo) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// Grouped launches: problem k of a descriptor array owns the global units
+// [gd[k].ubegin, gd[k + 1].ubegin); every warp role walks its units in
+// increasing order, so a forward-only cursor finds the problem of a unit.
+template <class D>
+__device__ __forceinline__ long long locate(const D* gd, int n, long long u, int& pid) {
+  while (pid + 1 < n && u >= gd[pid + 1].ubegin) ++pid;
+  return u - gd[pid].ubegin;
+}
+
 // Epilogue functor interface (b3_epilogues.cuh): a batched two-phase functor,
 // load(q, i, r, in) for kBatch elements, then store(q, i, r, re, im, in) for
 // each, so that the operand loads of a batch are in flight together.
+// one problem of a grouped fused launch (aligned as its tensor maps)
 template <class Epi>
+struct FusedDesc {
+  CUtensorMap xhi, xlo, mhi, mlo;
+  KParams kp;
+  long long ubegin;
+  Epi epi;
+};
+
+// Grouped form (G = true): one persistent launch serves the last mode
+// product of several independent problems; maps, sizes and the epilogue
+// functor of problem k come from gd[k].  Same arithmetic per unit.
+template <class Epi, bool G = false>
 __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
-                 const KParams kp, const Epi epi) {
+                 const KParams kp, const Epi epi, const FusedDesc<Epi>* __restrict__ gd, int ngd,
+                 long long gunits) {
   constexpr int NSTAGE = Cfg<Epi>::kStages;
   constexpr int NEPI = Cfg<Epi>::kEpi;
   constexpr uint32_t kOffEpi = Cfg<Epi>::kOffEpi;
@@ -226,37 +248,58 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const long long units = kp.tiles * kp.m_blocks;
-  const int KC = kp.k_chunks;
+  long long units;
+  int* err;
+  if constexpr (G) {
+    units = gunits;
+    err = gd[0].kp.err;
+  } else {
+    units = kp.tiles * kp.m_blocks;
+    err = kp.err;
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      int pid = 0;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const long long tile = u / kp.m_blocks;
-        const int mb = (int)(u % kp.m_blocks);
+        long long lu = u, R = kp.R;
+        int mbk = kp.m_blocks, KC = kp.k_chunks;
+        const CUtensorMap *mxh = &tm_xhi, *mxl = &tm_xlo, *mmh = &tm_mhi, *mml = &tm_mlo;
+        if constexpr (G) {
+          lu = locate(gd, ngd, u, pid);
+          R = gd[pid].kp.R;
+          mbk = gd[pid].kp.m_blocks;
+          KC = gd[pid].kp.k_chunks;
+          mxh = &gd[pid].xhi;
+          mxl = &gd[pid].xlo;
+          mmh = &gd[pid].mhi;
+          mml = &gd[pid].mlo;
+        }
+        const long long tile = lu / mbk;
+        const int mb = (int)(lu % mbk);
         const int r0 = (int)(tile * BR);
-        const int r1 = (int)(kp.R + tile * BR);   // same r in the imaginary plane
+        const int r1 = (int)(R + tile * BR);   // same r in the imaginary plane
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % NSTAGE);
           const uint32_t ph = (g / NSTAGE) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, kp.err, 1)) { ok = false; break; }
+          if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1)) { ok = false; break; }
           const uint32_t st = sbase + s * kStage;
           mbar_arrive_tx(full_bar(s), kStage);
-          tma_load_2d(st, &tm_mhi, kc * BK, mb * BM, full_bar(s));
-          tma_load_2d(st + 16384, &tm_mlo, kc * BK, mb * BM, full_bar(s));
-          tma_load_2d(st + 32768, &tm_xhi, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + 32768 + 8192, &tm_xhi, kc * BK, r1, full_bar(s));
-          tma_load_2d(st + 49152, &tm_xlo, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + 49152 + 8192, &tm_xlo, kc * BK, r1, full_bar(s));
+          tma_load_2d(st, mmh, kc * BK, mb * BM, full_bar(s));
+          tma_load_2d(st + 16384, mml, kc * BK, mb * BM, full_bar(s));
+          tma_load_2d(st + 32768, mxh, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 32768 + 8192, mxh, kc * BK, r1, full_bar(s));
+          tma_load_2d(st + 49152, mxl, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + 49152 + 8192, mxl, kc * BK, r1, full_bar(s));
         }
       }
       // drain: every issued stage must have landed before the CTA may exit
       const uint32_t issued = g;
       for (uint32_t q = issued >= NSTAGE ? issued - NSTAGE : 0; q < issued; ++q)
-        mbar_wait(full_bar(q % NSTAGE), (q / NSTAGE) & 1, abort_flag, kp.err, 7, true);
+        mbar_wait(full_bar(q % NSTAGE), (q / NSTAGE) & 1, abort_flag, err, 7, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -265,15 +308,21 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
                                  ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
       bool ok = true;
+      int pid = 0;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
+        int KC = kp.k_chunks;
+        if constexpr (G) {
+          locate(gd, ngd, u, pid);
+          KC = gd[pid].kp.k_chunks;
+        }
         const int a = t & 1;
-        if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, kp.err, 2)) break;
+        if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, err, 2)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + a * BN;
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % NSTAGE);
           const uint32_t ph = (g / NSTAGE) & 1;
-          if (!mbar_wait(full_bar(s), ph, abort_flag, kp.err, 3)) { ok = false; break; }
+          if (!mbar_wait(full_bar(s), ph, abort_flag, err, 3)) { ok = false; break; }
           tc_fence_after();
           const uint32_t ahi = sbase + s * kStage, alo = ahi + 16384;
           const uint32_t bhi = ahi + 32768, blo = ahi + 49152;
@@ -292,7 +341,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
       }
       // drain: all issued MMAs complete before TMEM is released
       mma_commit(fin_bar);
-      mbar_wait(fin_bar, 0, abort_flag, kp.err, 8, true);
+      mbar_wait(fin_bar, 0, abort_flag, err, 8, true);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -301,12 +350,24 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     float* stg = reinterpret_cast<float*>(smem + kOffEpi + (warp - 2) * kEpiWarp);
     const int rr = lane & 15, hrow = (lane >> 4) * 16;
     uint32_t t = 0;
+    int pid = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++t) {
       const int a = t & 1;
-      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, kp.err, 9)) break;
+      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, err, 9)) break;
       tc_fence_after();
-      const long long tile = u / kp.m_blocks;
-      const int mb = (int)(u % kp.m_blocks);
+      long long lu = u, Rl = kp.R;
+      int mbk = kp.m_blocks, pl = kp.p;
+      const Epi* Ep = &epi;
+      if constexpr (G) {
+        lu = locate(gd, ngd, u, pid);
+        Rl = gd[pid].kp.R;
+        mbk = gd[pid].kp.m_blocks;
+        pl = gd[pid].kp.p;
+        Ep = &gd[pid].epi;
+      }
+      const Epi& E = *Ep;
+      const long long tile = lu / mbk;
+      const int mb = (int)(lu % mbk);
       const int i_base = mb * BM + q * 32;
       // all of this warp's accumulator columns into registers, then hand the
       // accumulator back to the MMA warp before any store or functor work
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
           __syncwarp();
           constexpr int B = Epi::kBatch;
           constexpr int NI = Epi::kIn > 0 ? Epi::kIn : 1;
-          const uint32_t R32 = (uint32_t)kp.R;
+          const uint32_t R32 = (uint32_t)Rl;
           if ((R32 & 3u) == 0) {
             // 4 consecutive r per lane: lane = 4 a + k covers rows a, a + 8, .. and r = 16 cc + 4 k + 0..3
             const int k4 = lane & 3, a8 = lane >> 2;
@@ -346,20 +407,20 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
 #pragma unroll
               for (int b = 0; b < B; ++b) {
                 const int i = i_base + a8 + 8 * (it0 + b);
-                if (i < kp.p && r < R32) epi.template load<4>((uint32_t)i * R32 + r, i, r, in[b]);
+                if (i < pl && r < R32) E.template load<4>((uint32_t)i * R32 + r, i, r, in[b]);
               }
 #pragma unroll
               for (int b = 0; b < B; ++b) {
                 const int ii = a8 + 8 * (it0 + b);
                 const int i = i_base + ii;
-                if (i < kp.p && r < R32) {
+                if (i < pl && r < R32) {
                   float re[4], im[4];
 #pragma unroll
                   for (int v = 0; v < 4; ++v) {
                     re[v] = stg[ii * 33 + 4 * k4 + v];
                     im[v] = stg[ii * 33 + 16 + 4 * k4 + v];
                   }
-                  epi.template store<4>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
+                  E.template store<4>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
                 }
               }
             }
@@ -371,15 +432,15 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
 #pragma unroll
               for (int b = 0; b < B; ++b) {
                 const int i = i_base + it0 + b + hrow;
-                if (i < kp.p && r < R32) epi.template load<1>((uint32_t)i * R32 + r, i, r, in[b]);
+                if (i < pl && r < R32) E.template load<1>((uint32_t)i * R32 + r, i, r, in[b]);
               }
 #pragma unroll
               for (int b = 0; b < B; ++b) {
                 const int ii = it0 + b + hrow;
                 const int i = i_base + ii;
-                if (i < kp.p && r < R32) {
+                if (i < pl && r < R32) {
                   const float re[1] = {stg[ii * 33 + rr]}, im[1] = {stg[ii * 33 + 16 + rr]};
-                  epi.template store<1>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
+                  E.template store<1>((uint32_t)i * R32 + r, i, r, re, im, in[b]);
                 }
               }
             }

@@ -22,6 +22,12 @@
 //
 // Requirement (checked by the host): R % 8 == 0, the 16-byte row-pitch rule
 // of the output tensor maps.
+//
+// Grouped form (G = true): one persistent launch serves the plain mode
+// products of several independent problems (the instances of a batch); the
+// tensor maps and sizes of problem k come from the descriptor gd[k], which
+// owns the global units [gd[k].ubegin, gd[k + 1].ubegin).  The arithmetic per
+// unit is the same as in the single form.
 #pragma once
 
 #include "b3_kernel.cuh"
@@ -42,12 +48,19 @@ constexpr uint32_t kPlOffBar = kPlOffEpi + PL_NEPI * kPlEpiWarp;
 constexpr uint32_t kPlSmemBytes = kPlOffBar + 256 + 1024;   // + barriers + alignment slack
 static_assert(kPlSmemBytes <= 232448, "shared memory budget");
 
+// one problem of a grouped plain launch (aligned as its tensor maps)
+struct PlainDesc {
+  CUtensorMap xhi, xlo, mhi, mlo, yhi, ylo;
+  KParams kp;
+  long long ubegin;
+};
 
+template <bool G>
 __global__ void __launch_bounds__(PL_THREADS, 1)
     mp_b3_plain_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                        const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                        const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
-                       const KParams kp) {
+                       const KParams kp, const PlainDesc* __restrict__ gd, int ngd, long long gunits) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -92,52 +105,82 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const long long units = kp.tiles * kp.m_blocks;
-  const int KC = kp.k_chunks;
+  long long units;
+  int* err;
+  if constexpr (G) {
+    units = gunits;
+    err = gd[0].kp.err;
+  } else {
+    units = kp.tiles * kp.m_blocks;
+    err = kp.err;
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ X producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      int pid = 0;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const long long tile = u / kp.m_blocks;
+        long long lu = u, R = kp.R;
+        int mbk = kp.m_blocks, KC = kp.k_chunks;
+        const CUtensorMap *mxh = &tm_xhi, *mxl = &tm_xlo;
+        if constexpr (G) {
+          lu = locate(gd, ngd, u, pid);
+          R = gd[pid].kp.R;
+          mbk = gd[pid].kp.m_blocks;
+          KC = gd[pid].kp.k_chunks;
+          mxh = &gd[pid].xhi;
+          mxl = &gd[pid].xlo;
+        }
+        const long long tile = lu / mbk;
         const int r0 = (int)(tile * BR);
-        const int r1 = (int)(kp.R + tile * BR);   // same r in the imaginary plane
+        const int r1 = (int)(R + tile * BR);   // same r in the imaginary plane
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % PL_NX);
-          if (!mbar_wait(empty_x(s), ((g / PL_NX) & 1) ^ 1, abort_flag, kp.err, 11)) { ok = false; break; }
+          if (!mbar_wait(empty_x(s), ((g / PL_NX) & 1) ^ 1, abort_flag, err, 11)) { ok = false; break; }
           const uint32_t st = sbase + s * kXStage;
           mbar_arrive_tx(full_x(s), kXStage);
-          tma_load_2d(st, &tm_xhi, kc * BK, r0, full_x(s));
-          tma_load_2d(st + 8192, &tm_xhi, kc * BK, r1, full_x(s));
-          tma_load_2d(st + 16384, &tm_xlo, kc * BK, r0, full_x(s));
-          tma_load_2d(st + 24576, &tm_xlo, kc * BK, r1, full_x(s));
+          tma_load_2d(st, mxh, kc * BK, r0, full_x(s));
+          tma_load_2d(st + 8192, mxh, kc * BK, r1, full_x(s));
+          tma_load_2d(st + 16384, mxl, kc * BK, r0, full_x(s));
+          tma_load_2d(st + 24576, mxl, kc * BK, r1, full_x(s));
         }
       }
       const uint32_t issued = g;
       for (uint32_t q = issued >= PL_NX ? issued - PL_NX : 0; q < issued; ++q)
-        mbar_wait(full_x(q % PL_NX), (q / PL_NX) & 1, abort_flag, kp.err, 17, true);
+        mbar_wait(full_x(q % PL_NX), (q / PL_NX) & 1, abort_flag, err, 17, true);
     }
   } else if (warp == 2) {
     // ------------------------------------------------------------ M producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      int pid = 0;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const int mb = (int)(u % kp.m_blocks);
+        long long lu = u;
+        int mbk = kp.m_blocks, KC = kp.k_chunks;
+        const CUtensorMap *mmh = &tm_mhi, *mml = &tm_mlo;
+        if constexpr (G) {
+          lu = locate(gd, ngd, u, pid);
+          mbk = gd[pid].kp.m_blocks;
+          KC = gd[pid].kp.k_chunks;
+          mmh = &gd[pid].mhi;
+          mml = &gd[pid].mlo;
+        }
+        const int mb = (int)(lu % mbk);
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % PL_NM);
-          if (!mbar_wait(empty_m(s), ((g / PL_NM) & 1) ^ 1, abort_flag, kp.err, 12)) { ok = false; break; }
+          if (!mbar_wait(empty_m(s), ((g / PL_NM) & 1) ^ 1, abort_flag, err, 12)) { ok = false; break; }
           const uint32_t st = sbase + kPlOffM + s * kMStage;
           mbar_arrive_tx(full_m(s), kMStage);
-          tma_load_2d(st, &tm_mhi, kc * BK, mb * BM, full_m(s));
-          tma_load_2d(st + 16384, &tm_mlo, kc * BK, mb * BM, full_m(s));
+          tma_load_2d(st, mmh, kc * BK, mb * BM, full_m(s));
+          tma_load_2d(st + 16384, mml, kc * BK, mb * BM, full_m(s));
         }
       }
       const uint32_t issued = g;
       for (uint32_t q = issued >= PL_NM ? issued - PL_NM : 0; q < issued; ++q)
-        mbar_wait(full_m(q % PL_NM), (q / PL_NM) & 1, abort_flag, kp.err, 18, true);
+        mbar_wait(full_m(q % PL_NM), (q / PL_NM) & 1, abort_flag, err, 18, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -146,15 +189,21 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
                                  ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
       bool ok = true;
+      int pid = 0;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
+        int KC = kp.k_chunks;
+        if constexpr (G) {
+          locate(gd, ngd, u, pid);
+          KC = gd[pid].kp.k_chunks;
+        }
         const int a = t & 1;
-        if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, kp.err, 13)) break;
+        if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, err, 13)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + a * BN;
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int sx = (int)(g % PL_NX), sm = (int)(g % PL_NM);
-          if (!mbar_wait(full_m(sm), (g / PL_NM) & 1, abort_flag, kp.err, 14)) { ok = false; break; }
-          if (!mbar_wait(full_x(sx), (g / PL_NX) & 1, abort_flag, kp.err, 15)) { ok = false; break; }
+          if (!mbar_wait(full_m(sm), (g / PL_NM) & 1, abort_flag, err, 14)) { ok = false; break; }
+          if (!mbar_wait(full_x(sx), (g / PL_NX) & 1, abort_flag, err, 15)) { ok = false; break; }
           tc_fence_after();
           const uint32_t ahi = sbase + kPlOffM + sm * kMStage, alo = ahi + 16384;
           const uint32_t bhi = sbase + sx * kXStage, blo = bhi + 16384;
@@ -173,7 +222,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         mma_commit(acc_full(a));
       }
       mma_commit(fin_bar);
-      mbar_wait(fin_bar, 0, abort_flag, kp.err, 16, true);
+      mbar_wait(fin_bar, 0, abort_flag, err, 16, true);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -181,12 +230,22 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
     const int half = (warp - 3) >> 2;  // 16-column groups 2 half and 2 half + 1
     uint32_t* box = reinterpret_cast<uint32_t*>(smem + kPlOffEpi + (warp - 3) * kPlEpiWarp);
     uint32_t t = 0;
+    int pid = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++t) {
       const int a = t & 1;
-      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, kp.err, 19)) break;
+      if (!mbar_wait(acc_full(a), (t >> 1) & 1, abort_flag, err, 19)) break;
       tc_fence_after();
-      const long long tile = u / kp.m_blocks;
-      const int mb = (int)(u % kp.m_blocks);
+      long long lu = u;
+      int mbk = kp.m_blocks;
+      const CUtensorMap *myh = &tm_yhi, *myl = &tm_ylo;
+      if constexpr (G) {
+        lu = locate(gd, ngd, u, pid);
+        mbk = gd[pid].kp.m_blocks;
+        myh = &gd[pid].yhi;
+        myl = &gd[pid].ylo;
+      }
+      const long long tile = lu / mbk;
+      const int mb = (int)(lu % mbk);
       uint32_t vr[2][16], vi[2][16];
 #pragma unroll
       for (int g2 = 0; g2 < 2; ++g2) {
@@ -226,8 +285,8 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         if (lane == 0) {
           const int x = (int)(tile * BR + 32 * half);
           const uint32_t sb = smem_u32(box);
-          tma_store_3d(&tm_yhi, sb, x, i_base, comp);
-          tma_store_3d(&tm_ylo, sb + 2048, x, i_base, comp);
+          tma_store_3d(myh, sb, x, i_base, comp);
+          tma_store_3d(myl, sb + 2048, x, i_base, comp);
           bulk_commit();
         }
         __syncwarp();

@@ -34,6 +34,21 @@ struct fcgle_batch_ctx {
   std::vector<cudaEvent_t> join;
   std::map<std::pair<int, uint64_t>, cudaGraphExec_t> graphs;
   long long graph_launches = 0;
+  // grouped persistent launches: per (scheme, tau) the phases of one step,
+  // each one launch over the descriptors of all instances in that phase
+  struct Phase {
+    void (*launch)(const void*, int, long long, cudaStream_t);
+    size_t offset;     // of its descriptor array in dev
+    int n;
+    long long units;
+  };
+  struct Plan {
+    std::vector<Phase> phases;
+    void* dev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+  };
+  std::map<std::pair<int, uint64_t>, Plan> plans;
+  long long grouped_kernels = 0;
 };
 
 namespace fcgle {
@@ -311,6 +326,10 @@ static void batch_free(fcgle_batch_ctx* b) {
   if (!b) return;
   if (b->origin) cudaStreamSynchronize(b->origin);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : b->plans) {
+    if (kv.second.graph) cudaGraphExecDestroy(kv.second.graph);
+    if (kv.second.dev) cudaFree(kv.second.dev);
+  }
   for (auto* h : b->inst) delete h;
   for (auto st : b->streams) {
     cudaStreamSynchronize(st);
@@ -405,6 +424,82 @@ fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h) {
   });
 }
 
+// Record step `n` of every instance and group the records into phases: for
+// each Tucker operator of the step, the k-th inner mode product of all
+// instances (k = 0, 1, ..), then the last mode products; records of one phase
+// with the same kernel type share a launch.  Returns false (nothing built) if
+// an instance has no grouped form.
+static bool build_plan(fcgle_batch_ctx* b, int n, cudaStream_t st, fcgle_batch_ctx::Plan& plan) {
+  const int ni = (int)b->inst.size();
+  std::vector<std::vector<fcgle::GroupRec>> recs(ni);
+  bool ok = true;
+  for (int i = 0; i < ni && ok; ++i) {
+    if (!b->inst[i]->eng->set_recorder(&recs[i])) {
+      ok = false;
+      break;
+    }
+    try {
+      b->inst[i]->eng->one_step(n);
+    } catch (...) {
+      b->inst[i]->eng->set_recorder(nullptr);
+      throw;
+    }
+    b->inst[i]->eng->set_recorder(nullptr);
+  }
+  if (!ok) return false;
+  // split each instance's records into Tucker operators (each ends with a `last` record)
+  std::vector<std::vector<std::vector<const fcgle::GroupRec*>>> tk(ni);
+  for (int i = 0; i < ni; ++i) {
+    std::vector<const fcgle::GroupRec*> cur;
+    for (const auto& r : recs[i]) {
+      cur.push_back(&r);
+      if (r.last) {
+        tk[i].push_back(cur);
+        cur.clear();
+      }
+    }
+    if (!cur.empty() || tk[i].size() != tk[0].size()) return false;
+  }
+  std::vector<uint8_t> host;
+  auto add_phase = [&](const std::vector<const fcgle::GroupRec*>& rs) {
+    // one launch per kernel type among rs, in first-appearance order
+    std::vector<void (*)(const void*, int, long long, cudaStream_t)> kinds;
+    for (auto* r : rs)
+      if (std::find(kinds.begin(), kinds.end(), r->launch) == kinds.end()) kinds.push_back(r->launch);
+    for (auto fn : kinds) {
+      fcgle_batch_ctx::Phase ph{fn, (host.size() + 255) / 256 * 256, 0, 0};
+      host.resize(ph.offset);
+      for (auto* r : rs) {
+        if (r->launch != fn) continue;
+        const size_t at = host.size();
+        host.insert(host.end(), r->desc.begin(), r->desc.end());
+        std::memcpy(host.data() + at + r->ubegin_off, &ph.units, sizeof(long long));
+        ph.units += r->units;
+        ++ph.n;
+      }
+      plan.phases.push_back(ph);
+    }
+  };
+  const size_t nt = tk[0].size();
+  for (size_t t = 0; t < nt; ++t) {
+    size_t inner = 0;
+    for (int i = 0; i < ni; ++i) inner = std::max(inner, tk[i][t].size() - 1);
+    for (size_t k = 0; k < inner; ++k) {
+      std::vector<const fcgle::GroupRec*> rs;
+      for (int i = 0; i < ni; ++i)
+        if (k + 1 < tk[i][t].size()) rs.push_back(tk[i][t][k]);
+      add_phase(rs);
+    }
+    std::vector<const fcgle::GroupRec*> last;
+    for (int i = 0; i < ni; ++i) last.push_back(tk[i][t].back());
+    add_phase(last);
+  }
+  FCGLE_CUDA(cudaMalloc(&plan.dev, std::max<size_t>(host.size(), 256)));
+  FCGLE_CUDA(cudaMemcpyAsync(plan.dev, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+  FCGLE_CUDA(cudaStreamSynchronize(st));
+  return true;
+}
+
 fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,
                                    const void* const* u0, void* const* uT, int use_graph) {
   return guarded([&] {
@@ -438,7 +533,52 @@ fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int ns
       for (int i = 0; i < n; ++i) b->inst[i]->eng->one_step(0);
       first = 1;
     }
-    if (replay && first < nsteps) {
+    bool grouped_done = false;
+    if (use_graph == 2 && replay && first < nsteps) {
+      join();
+      uint64_t tb;
+      std::memcpy(&tb, &tau, 8);
+      const auto key = std::make_pair(scheme, tb);
+      auto it = b->plans.find(key);
+      if (it == b->plans.end()) {
+        fcgle_batch_ctx::Plan plan;
+        bool built = false;
+        try {
+          built = build_plan(b, first, b->origin, plan);
+          if (built) {
+            cudaGraph_t g = nullptr;
+            FCGLE_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+            try {
+              for (const auto& ph : plan.phases)
+                ph.launch(static_cast<const uint8_t*>(plan.dev) + ph.offset, ph.n, ph.units, b->origin);
+            } catch (...) {
+              cudaStreamEndCapture(b->origin, &g);
+              if (g) cudaGraphDestroy(g);
+              throw;
+            }
+            FCGLE_CUDA(cudaStreamEndCapture(b->origin, &g));
+            cudaError_t e = cudaGraphInstantiate(&plan.graph, g, 0);
+            cudaGraphDestroy(g);
+            FCGLE_CUDA(e);
+          }
+        } catch (...) {
+          if (plan.dev) cudaFree(plan.dev);
+          throw;
+        }
+        if (built) it = b->plans.emplace(key, plan).first;
+      }
+      if (it != b->plans.end()) {
+        for (int k = first; k < nsteps; ++k) {
+          FCGLE_CUDA(cudaGraphLaunch(it->second.graph, b->origin));
+          ++b->graph_launches;
+          b->grouped_kernels += (long long)it->second.phases.size();
+        }
+        grouped_done = true;
+      }
+      fork();
+    }
+    if (grouped_done) {
+    } else if (replay && first < nsteps) {
       join();
       uint64_t tb;
       std::memcpy(&tb, &tau, 8);
@@ -484,6 +624,7 @@ fcgle_status fcgle_batch_launch_count(fcgle_batch b, long long* kernels, long lo
     if (!b) throw InvalidArg("NULL batch");
     long long k = 0;
     for (auto* h : b->inst) k += h->eng->launches;
+    k += b->grouped_kernels;
     if (kernels) *kernels = k;
     if (graph_launches) *graph_launches = b->graph_launches;
   });

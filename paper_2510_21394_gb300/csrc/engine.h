@@ -67,7 +67,22 @@ class EngineBase {
   virtual bool time_dependent() const = 0;
   virtual size_t elem_bytes() const = 0;
   virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
+  // Grouped batch launches: while a recorder is set, every mode product of
+  // one_step is recorded (as a kernel descriptor) instead of launched.
+  // Returns false if the engine has no grouped form (FP64, d == 1).
+  virtual bool set_recorder(std::vector<struct GroupRec>* rec) { return rec == nullptr; }
   long long launches = 0;
+};
+
+// One recorded mode product: the descriptor of one problem of a grouped
+// persistent launch, and the launcher of that kernel type.  Records with the
+// same launcher can share a launch (their descriptors concatenated).
+struct GroupRec {
+  bool last;   // last mode product of a Tucker operator (carries the scheme's epilogue)
+  void (*launch)(const void* descs, int n, long long units, cudaStream_t st);
+  size_t ubegin_off;          // byte offset of the descriptor's first-unit field
+  std::vector<uint8_t> desc;  // the descriptor bytes (size = stride in the array)
+  long long units;
 };
 
 // D_mu of direction mu (Eq. Dnalpha / Eq. FD4) and its FP64 eigendecomposition

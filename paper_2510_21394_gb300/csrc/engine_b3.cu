@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstddef>
 #include <complex>
 #include <cstring>
 #include <map>
@@ -245,7 +246,7 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiLRK2A>();
       set_smem_attr<b3::EpiLRK2B>();
       set_smem_attr<b3::EpiStrangB>();
-      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
       attrs = true;
     }
@@ -437,7 +438,7 @@ class EngineB3 : public EngineBase {
 
   template <class Epi>
   static void set_smem_attr() {
-    FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)b3::Cfg<Epi>::kSmemBytes));
   }
 
@@ -508,9 +509,65 @@ class EngineB3 : public EngineBase {
     CUtensorMap tyh, tyl;
     encode_bf16_out(&tyh, out.hi, (uint64_t)R, (uint64_t)s_.p[mu]);
     encode_bf16_out(&tyl, out.lo, (uint64_t)R, (uint64_t)s_.p[mu]);
-    b3::mp_b3_plain_kernel<<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st_>>>(txh, txl, m.tm_hi, m.tm_lo, tyh, tyl,
-                                                                             kp);
+    if (rec_) {
+      b3::PlainDesc d;
+      std::memset(&d, 0, sizeof(d));
+      d.xhi = txh;
+      d.xlo = txl;
+      d.mhi = m.tm_hi;
+      d.mlo = m.tm_lo;
+      d.yhi = tyh;
+      d.ylo = tyl;
+      d.kp = kp;
+      record(false, &launch_plain_grouped, offsetof(b3::PlainDesc, ubegin), &d, sizeof(d), units);
+      return;
+    }
+    b3::mp_b3_plain_kernel<false><<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st_>>>(
+        txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, nullptr, 0, 0);
     FCGLE_LAUNCHED(launches);
+  }
+
+  // ---- grouped launches (batches): recording and the launchers
+  void record(bool last, void (*fn)(const void*, int, long long, cudaStream_t), size_t uoff, const void* d,
+              size_t bytes, long long units) {
+    GroupRec r;
+    r.last = last;
+    r.launch = fn;
+    r.ubegin_off = uoff;
+    r.desc.assign((const uint8_t*)d, (const uint8_t*)d + bytes);
+    r.units = units;
+    rec_->push_back(std::move(r));
+  }
+  static void launch_plain_grouped(const void* descs, int n, long long units, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b3::kPlSmemBytes));
+      attr = true;
+    }
+    CUtensorMap z;
+    std::memset(&z, 0, sizeof(z));
+    b3::KParams kp{};
+    const int grid = (int)std::min<long long>(units, num_sms());
+    b3::mp_b3_plain_kernel<true><<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st>>>(
+        z, z, z, z, z, z, kp, static_cast<const b3::PlainDesc*>(descs), n, units);
+    FCGLE_CUDA(cudaGetLastError());
+  }
+  template <class Epi>
+  static void launch_fused_grouped(const void* descs, int n, long long units, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b3::Cfg<Epi>::kSmemBytes));
+      attr = true;
+    }
+    CUtensorMap z;
+    std::memset(&z, 0, sizeof(z));
+    b3::KParams kp{};
+    const int grid = (int)std::min<long long>(units, num_sms());
+    b3::mp_b3_kernel<Epi, true><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st>>>(
+        z, z, z, z, kp, Epi{}, static_cast<const b3::FusedDesc<Epi>*>(descs), n, units);
+    FCGLE_CUDA(cudaGetLastError());
   }
 
   // one mode product of direction mu on split input (xh, xl) with epilogue epi
@@ -530,8 +587,20 @@ class EngineB3 : public EngineBase {
     kp.err = err_->ptr;
     const long long units = kp.tiles * kp.m_blocks;
     const int grid = (int)std::min<long long>(units, num_sms());
-    b3::mp_b3_kernel<Epi><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_>>>(
-        txh, txl, m.tm_hi, m.tm_lo, kp, epi);
+    if (rec_) {
+      b3::FusedDesc<Epi> d;
+      std::memset(static_cast<void*>(&d), 0, sizeof(d));
+      d.xhi = txh;
+      d.xlo = txl;
+      d.mhi = m.tm_hi;
+      d.mlo = m.tm_lo;
+      d.kp = kp;
+      d.epi = epi;
+      record(last_mp_, &launch_fused_grouped<Epi>, offsetof(b3::FusedDesc<Epi>, ubegin), &d, sizeof(d), units);
+      return;
+    }
+    b3::mp_b3_kernel<Epi, false><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_>>>(
+        txh, txl, m.tm_hi, m.tm_lo, kp, epi, nullptr, 0, 0);
     FCGLE_LAUNCHED(launches);
   }
 
@@ -552,7 +621,9 @@ class EngineB3 : public EngineBase {
       store_split(src.hi, src.lo, mu, fwd, dst);
       src = dst;
     }
+    last_mp_ = true;
     launch_mp(src.hi, src.lo, d - 1, fwd, epi);
+    last_mp_ = false;
   }
 
   void pack_f32(const float* user, float* U) { pack<float>(s_, user, U, st_, launches); }
@@ -752,6 +823,13 @@ class EngineB3 : public EngineBase {
     unpack_f32(F32(kU), (float*)uT);
   }
   bool time_dependent() const override { return gs_.nsrc > 0; }
+  bool set_recorder(std::vector<GroupRec>* rec) override {
+    if (rec && s_.d < 2) return false;   // d == 1 copies the input aside inside a Tucker operator
+    rec_ = rec;
+    return true;
+  }
+  std::vector<GroupRec>* rec_ = nullptr;
+  bool last_mp_ = false;
 
   int rs_scheme_ = 0;
   double rs_tau_ = 0.0, rs_t0_ = 0.0;

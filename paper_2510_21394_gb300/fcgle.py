@@ -169,7 +169,7 @@ def fcgle_batch_integrate(b, scheme, tau, nsteps, t0, u0_list, uT_list, use_grap
     n = len(u0_list)
     a = (ctypes.c_void_p * n)(*[_ptr(t).value for t in u0_list])
     o = (ctypes.c_void_p * n)(*[_ptr(t).value for t in uT_list])
-    _check(_lib.fcgle_batch_integrate(b, scheme, float(tau), int(nsteps), float(t0), a, o, int(bool(use_graph))))
+    _check(_lib.fcgle_batch_integrate(b, scheme, float(tau), int(nsteps), float(t0), a, o, int(use_graph)))
 
 
 def fcgle_batch_launch_count(b):
@@ -379,9 +379,11 @@ class Batch:
     def instance(self, i):
         return fcgle_batch_instance(self.b, i)
 
-    def integrate(self, scheme, tau, nsteps, u0_list, t0=0.0, out=None, use_graph=True):
+    def integrate(self, scheme, tau, nsteps, u0_list, t0=0.0, out=None, use_graph=True, grouped=False):
+        """grouped=True: one persistent launch per phase of a step over all instances."""
         out = [torch.empty_like(u) for u in u0_list] if out is None else out
-        fcgle_batch_integrate(self.b, scheme, tau, nsteps, t0, u0_list, out, use_graph)
+        mode = 2 if grouped else (1 if use_graph else 0)
+        fcgle_batch_integrate(self.b, scheme, tau, nsteps, t0, u0_list, out, mode)
         return out
 
     def launches(self):

@@ -34,7 +34,7 @@ def fc():
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
 @pytest.mark.parametrize("scheme", ["etd2rk", "lbdf2", "krogstad"])
-@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("graph", [True, False, "grouped"])
 def test_batch_equals_single_runs(fc, prec, scheme, graph):
     specs = _specs()
     dt = torch.complex64 if prec == "bf16x3" else torch.complex128
@@ -42,11 +42,19 @@ def test_batch_equals_single_runs(fc, prec, scheme, graph):
     u0 = [torch.from_numpy(inputs.gaussian_pulse(sp["ns"], [(-3.0, 3.0)] * len(sp["ns"]))).to(dt).cuda()
           for sp in specs]
     tau, m = 5e-3, 6
-    outs = b.integrate(scheme, tau, m, u0, use_graph=graph)
-    outs2 = b.integrate(scheme, tau, m, u0, use_graph=graph)   # cached graph, same result
+    grouped = graph == "grouped"
+    use_graph = bool(graph)
+    k0, _ = b.launches()
+    outs = b.integrate(scheme, tau, m, u0, use_graph=use_graph, grouped=grouped)
+    outs2 = b.integrate(scheme, tau, m, u0, use_graph=use_graph, grouped=grouped)   # cached plan, same result
     torch.cuda.synchronize()
     k, gl = b.launches()
-    assert k > 0 and (gl > 0) == (graph)
+    assert k > 0 and (gl > 0) == use_graph
+    if grouped and prec == "bf16x3":
+        # grouped: a step of all 7 instances is a few launches (3 per Tucker operator of
+        # this 2D + 3D mix), not one per instance and mode product
+        steps = 2 * (m - (1 if scheme == "lbdf2" else 0))
+        assert gl == steps
     for sp, u, o, o2 in zip(specs, u0, outs, outs2):
         s = fc.Solver(sp["ns"], sp["boxes"], sp["alphas"], sp["nu"], sp["eta"], sp["gamma"], sp["kappa"],
                       sp["zeta"], precision=prec)

@@ -88,6 +88,10 @@ def test_config4_batched_96_instances(fc):
     o32 = b32.integrate("etd2rk", 1e-3, 100, [x.to(torch.complex64) for x in u0], use_graph=True)
     torch.cuda.synchronize()
     assert b32.launches()[1] == 100
+    # grouped persistent launches (one per phase over all 96 instances): bitwise the same
+    og = b32.integrate("etd2rk", 1e-3, 100, [x.to(torch.complex64) for x in u0], grouped=True)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, c) for a, c in zip(o32, og))
     sample = list(range(0, 96, 6))
     b64 = fc.Batch([specs[i] for i in sample], precision="fp64")
     o64 = b64.integrate("etd2rk", 1e-3, 100, [u0[i] for i in sample])
