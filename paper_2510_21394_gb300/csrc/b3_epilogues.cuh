@@ -439,7 +439,7 @@ struct EpiStageD {
 // G^ = product;  F^ = Lam o U^ + G^ -> Fh;  S = c phi_1(theta Lam) o F^ -> split;
 // optionally U^ += S
 struct EpiFhat {
-  FCGLE_EPI(2, 4)
+  FCGLE_EPI(2, 2)
   uint32_t P;
   LamF L;
   float* Uh;
@@ -493,7 +493,7 @@ struct EpiFhat {
 // Krogstad stage 2 (Eq. krogstad-m), zh = tau/2 Lam:
 // D^_2 = product -> D2;  S = tau (1/2 phi_1(zh) F^ + phi_2(zh) D^_2) -> split
 struct EpiKrog2 {
-  FCGLE_EPI(2, 4)
+  FCGLE_EPI(2, 2)
   uint32_t P;
   LamF L;
   const float* Fh;
