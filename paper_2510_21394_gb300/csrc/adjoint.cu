@@ -11,13 +11,12 @@ namespace fcgle {
 namespace {
 
 int grid_of(size_t n) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {   // thread-safe one-time initialisation
+    int dev = 0, m = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 132;
-  }
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    return m > 0 ? m : 132;
+  }();
   size_t g = (n + 255) / 256;
   if (g > (size_t)sms * 8) g = (size_t)sms * 8;
   return (int)(g < 1 ? 1 : g);

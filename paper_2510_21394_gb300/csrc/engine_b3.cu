@@ -22,6 +22,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -50,12 +51,12 @@ struct DevMem {
 };
 
 int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {   // thread-safe one-time initialisation
+    int dev = 0, m = 0;
     FCGLE_CUDA(cudaGetDevice(&dev));
-    FCGLE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+    FCGLE_CUDA(cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev));
+    return m;
+  }();
   return sms;
 }
 
@@ -228,8 +229,10 @@ class EngineB3 : public EngineBase {
     err_.reset(new DevMem<int>(1));
     FCGLE_CUDA(cudaMemsetAsync(err_->ptr, 0, sizeof(int), st_));
     FCGLE_CUDA(cudaStreamSynchronize(st_));
-    static bool attrs = false;
-    if (!attrs) {
+    // once per process (instances of a batch are set up in parallel threads);
+    // an exception leaves the flag unset, so a later setup retries
+    static std::once_flag attrs;
+    std::call_once(attrs, [] {
       set_smem_attr<b3::EpiStoreSplitGen>();
       set_smem_attr<b3::EpiStoreF32>();
       set_smem_attr<b3::EpiScaleF>();
@@ -248,8 +251,7 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiStrangB>();
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
-      attrs = true;
-    }
+    });
   }
 
   ~EngineB3() override {
@@ -539,12 +541,11 @@ class EngineB3 : public EngineBase {
     rec_->push_back(std::move(r));
   }
   static void launch_plain_grouped(const void* descs, int n, long long units, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
-      attr = true;
-    }
+    });
     CUtensorMap z;
     std::memset(&z, 0, sizeof(z));
     b3::KParams kp{};
@@ -555,12 +556,11 @@ class EngineB3 : public EngineBase {
   }
   template <class Epi>
   static void launch_fused_grouped(const void* descs, int n, long long units, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::Cfg<Epi>::kSmemBytes));
-      attr = true;
-    }
+    });
     CUtensorMap z;
     std::memset(&z, 0, sizeof(z));
     b3::KParams kp{};
