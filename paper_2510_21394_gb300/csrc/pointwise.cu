@@ -16,13 +16,12 @@ namespace {
 
 inline int grid_for(size_t work, int block) {
   size_t g = (work + block - 1) / block;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {   // thread-safe one-time initialisation
+    int dev = 0, m = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 132;
-  }
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    return m > 0 ? m : 132;
+  }();
   size_t cap = (size_t)sms * 16;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
