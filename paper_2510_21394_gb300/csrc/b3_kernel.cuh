@@ -77,6 +77,16 @@ struct KParams {
 };
 
 // -------------------------------------------------------------- PTX helpers
+// Programmatic dependent launch.  Every mode-product kernel lets the next
+// kernel of its stream be scheduled as soon as all of its own CTAs are running
+// (pdl_trigger at entry) and, after its prologue (mbarrier init, TMEM
+// allocation), waits until the previous kernel of the stream has completed and
+// its writes are visible (pdl_wait) before it touches global memory.  The
+// wait ends when that kernel ends; without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -212,6 +222,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
   constexpr uint32_t kOffEpi = Cfg<Epi>::kOffEpi;
   constexpr uint32_t kOffBar = Cfg<Epi>::kOffBar;
   extern __shared__ uint8_t smem_raw[];
+  pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -247,6 +258,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();
 
   long long units;
   int* err;

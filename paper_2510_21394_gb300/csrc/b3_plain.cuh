@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
                        const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                        const KParams kp, const PlainDesc* __restrict__ gd, int ngd, long long gunits) {
   extern __shared__ uint8_t smem_raw[];
+  pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();
 
   long long units;
   int* err;

@@ -20,7 +20,9 @@
 #include <cmath>
 #include <cstddef>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -49,6 +51,33 @@ struct DevMem {
   DevMem(const DevMem&) = delete;
   DevMem& operator=(const DevMem&) = delete;
 };
+
+// Programmatic dependent launch of the mode-product kernels (on unless the
+// environment sets FCGLE_PDL=0): the kernel may be scheduled while the previous
+// kernel of the stream drains and runs its prologue meanwhile; it waits for
+// that kernel's completion (griddepcontrol.wait) before any global access.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("FCGLE_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <class... P, class... A>
+void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  FCGLE_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...));
+}
 
 int num_sms() {
   static const int sms = [] {   // thread-safe one-time initialisation
@@ -524,8 +553,8 @@ class EngineB3 : public EngineBase {
       record(false, &launch_plain_grouped, offsetof(b3::PlainDesc, ubegin), &d, sizeof(d), units);
       return;
     }
-    b3::mp_b3_plain_kernel<false><<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st_>>>(
-        txh, txl, m.tm_hi, m.tm_lo, tyh, tyl, kp, nullptr, 0, 0);
+    launch_pdl(b3::mp_b3_plain_kernel<false>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl, m.tm_hi,
+               m.tm_lo, tyh, tyl, kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
     FCGLE_LAUNCHED(launches);
   }
 
@@ -550,9 +579,8 @@ class EngineB3 : public EngineBase {
     std::memset(&z, 0, sizeof(z));
     b3::KParams kp{};
     const int grid = (int)std::min<long long>(units, num_sms());
-    b3::mp_b3_plain_kernel<true><<<grid, b3::PL_THREADS, b3::kPlSmemBytes, st>>>(
-        z, z, z, z, z, z, kp, static_cast<const b3::PlainDesc*>(descs), n, units);
-    FCGLE_CUDA(cudaGetLastError());
+    launch_pdl(b3::mp_b3_plain_kernel<true>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st, z, z, z, z, z, z, kp,
+               static_cast<const b3::PlainDesc*>(descs), n, units);
   }
   template <class Epi>
   static void launch_fused_grouped(const void* descs, int n, long long units, cudaStream_t st) {
@@ -565,9 +593,8 @@ class EngineB3 : public EngineBase {
     std::memset(&z, 0, sizeof(z));
     b3::KParams kp{};
     const int grid = (int)std::min<long long>(units, num_sms());
-    b3::mp_b3_kernel<Epi, true><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st>>>(
-        z, z, z, z, kp, Epi{}, static_cast<const b3::FusedDesc<Epi>*>(descs), n, units);
-    FCGLE_CUDA(cudaGetLastError());
+    launch_pdl(b3::mp_b3_kernel<Epi, true>, grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st, z, z, z, z,
+               kp, Epi{}, static_cast<const b3::FusedDesc<Epi>*>(descs), n, units);
   }
 
   // one mode product of direction mu on split input (xh, xl) with epilogue epi
@@ -599,8 +626,8 @@ class EngineB3 : public EngineBase {
       record(last_mp_, &launch_fused_grouped<Epi>, offsetof(b3::FusedDesc<Epi>, ubegin), &d, sizeof(d), units);
       return;
     }
-    b3::mp_b3_kernel<Epi, false><<<grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_>>>(
-        txh, txl, m.tm_hi, m.tm_lo, kp, epi, nullptr, 0, 0);
+    launch_pdl(b3::mp_b3_kernel<Epi, false>, grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_, txh, txl,
+               m.tm_hi, m.tm_lo, kp, epi, (const b3::FusedDesc<Epi>*)nullptr, 0, 0LL);
     FCGLE_LAUNCHED(launches);
   }
 
