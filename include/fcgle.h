@@ -27,6 +27,12 @@
  * Streams.  Every device entry point is asynchronous on the handle's CUDA
  *   stream (given at setup, changeable with fcgle_set_stream); the caller
  *   synchronises.  _host entry points synchronise before returning.
+ *   The tensor-core mode-product kernels of FCGLE_BF16X3 handles are launched
+ *   with programmatic dependent launch: each may start its prologue while the
+ *   previous kernel of the stream drains and waits for that kernel's
+ *   completion before touching global memory, so stream order is kept.  The
+ *   environment variable FCGLE_PDL=0, read once per process, launches them
+ *   plainly instead (same kernels, bitwise the same results).
  * Errors.  Every function returns an fcgle_status; nothing throws across the
  *   ABI.  On error, fcgle_last_error() returns a thread-local message.
  *   Invalid parameters (d not in 1..3, n_mu < 1, alpha_mu not in (1,2),
