@@ -34,6 +34,14 @@ ALPHAS = [1.2, 1.5, 1.8]
 PARS = dict(nu=1.0, eta=0.5, gamma=1.0, kappa=1.0, zeta=0.5)
 TAU = 1e-3
 KROGSTAD_BYTES_PER_ELEM = 16 * 16 + 32 + 3 * 24 + 32 + 40 + 40 + 24   # 496 B per complex element
+
+
+def etd2rk_bytes_per_elem(d):
+    """Algorithmic bytes per complex element of one split-BF16 ETD2RK step in d
+    dimensions: 4 Tucker operators of d - 1 plain mode products (16 B each) and
+    the epilogues of their last products (EpiFhat without F^: X, U^ read, S, U^
+    written, 32 B; EpiStageD 24; EpiEtd2 32; EpiUpdateG 24)."""
+    return 4 * 16 * (d - 1) + 32 + 24 + 32 + 24
 METRIC = "DoF*steps/s"
 UNIT = "DoF*steps/s"
 
@@ -500,10 +508,17 @@ def run_batched(args, rank, world, local_rank):
         except Exception as e:
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     if rank == 0:
+        # the whole grouped step against HBM, over the instances' grid points
+        peak, peak_kind = measured_peaks()
+        step_bytes = sum(etd2rk_bytes_per_elem(len(sp["ns"])) * int(np.prod(sp["ns"])) for sp in specs)
+        step_gbs = step_bytes / (r["ms"] / args.steps / 1e3) / 1e9
+        step_roof = {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_gbs / peak, 4), "floor_ms": round(step_bytes / (peak * 1e9) * 1e3, 4),
+                     "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
         line = {"metric": METRIC, "value": aggregate_rate(dof, args.steps, r["ms"] / 1e3, world), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
-                "data": "synthetic", "config": batched_config(specs, True),
+                "data": "synthetic", "config": batched_config(specs, True), "step_roofline": step_roof,
                 "e2e": {"value": aggregate_rate(dof, args.steps, e2e_s, world), "unit": UNIT,
                         "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                         "note": "all u0 copied in from pinned memory and all u(T) copied out per call of K steps"},

@@ -436,8 +436,8 @@ struct EpiStageD {
   }
 };
 
-// G^ = product;  F^ = Lam o U^ + G^ -> Fh;  S = c phi_1(theta Lam) o F^ -> split;
-// optionally U^ += S
+// G^ = product;  F^ = Lam o U^ + G^ -> Fh (not stored when Fh is null: ETD2RK
+// needs F^ only here);  S = c phi_1(theta Lam) o F^ -> split;  optionally U^ += S
 struct EpiFhat {
   FCGLE_EPI(2, 2)
   uint32_t P;
@@ -475,8 +475,10 @@ struct EpiFhat {
       sr[v] = c * (pr[0] * fr[v] - pi[0] * fi[v]);
       si[v] = c * (pr[0] * fi[v] + pi[0] * fr[v]);
     }
-    stv<V>(Fh + q, fr);
-    stv<V>(Fh + P + q, fi);
+    if (Fh) {
+      stv<V>(Fh + q, fr);
+      stv<V>(Fh + P + q, fi);
+    }
     put_csplit<V>(S, P, q, sr, si);
     if (update_uh) {
 #pragma unroll

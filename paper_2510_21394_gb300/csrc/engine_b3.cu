@@ -805,9 +805,9 @@ class EngineB3 : public EngineBase {
         break;
       }
       case FCGLE_ETD2RK: {
-        float *Uh = F32(kUh), *Fh = F32(kFh);
-        // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1
-        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, Fh, ft, ft, 1, V, phipoly(tau)});
+        float* Uh = F32(kUh);
+        // S1 = tau phi_1(tau Lam) o (Lam o U^ + G^);  a^ = U^ + S1 (F^ itself is not needed later)
+        tucker(V, true, b3::EpiFhat{P32(), lf_, Uh, nullptr, ft, ft, 1, V, phipoly(tau)});
         // a = u + bwd(S1);  D = g(t + tau, a) - g(t, u)
         tucker(V, false, b3::EpiStageD{P32(), U, nullptr, gs_, gtime(t + tau), gtime(t), V});
         // U^_{n+1} = a^ + tau phi_2(tau Lam) o D^
