@@ -213,6 +213,24 @@ fcgle_status fcgle_norm_static(const fcgle_params* p, const void* u, void* cuda_
  * an asynchronous CUDA error. */
 fcgle_status fcgle_sync(fcgle_handle h);
 
+/* Self-test of the bounded device-side waits (a library facility, not a step
+ * of the method).  Every mbarrier wait of the tensor-core kernels is bounded
+ * by a 2 s wall-clock limit, after which the kernel records a code in a device
+ * error word and returns, so that the context stays usable and the host can
+ * report FCGLE_ERR_TIMEOUT (see fcgle_sync).  This call runs that same wait on
+ * an mbarrier that nothing ever completes (one warp, no data), then a second
+ * kernel on the same stream, and synchronises the stream; it takes about 2 s.
+ *
+ * cuda_stream: a cudaStream_t (NULL: the legacy default stream).
+ * code_out:    receives the code the wait recorded (99 for this wait).
+ *
+ * Returns FCGLE_ERR_TIMEOUT with *code_out = 99 when the wait gave up at its
+ * limit, reported it, and the follow-up kernel ran: the expected outcome.
+ * Any other status means the mechanism failed (FCGLE_ERR_CUDA if the wait
+ * completed or the follow-up did not run); NULL code_out gives
+ * FCGLE_ERR_INVALID_ARG before anything runs. */
+fcgle_status fcgle_selftest_bounded_wait(void* cuda_stream, int* code_out);
+
 /* Sizes: N (complex elements of a user tensor) and the bytes of one user
  * tensor. */
 fcgle_status fcgle_sizes(fcgle_handle h, size_t* n_elems, size_t* n_bytes);

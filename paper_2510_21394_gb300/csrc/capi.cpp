@@ -13,6 +13,7 @@
 
 #include "engine.h"
 #include "norm_static.h"
+#include "selftest.h"
 
 struct fcgle_ctx {
   fcgle_params prm;
@@ -267,6 +268,16 @@ fcgle_status fcgle_norm_static(const fcgle_params* p, const void* u, void* cuda_
     if (p->precision != FCGLE_FP64 && p->precision != FCGLE_BF16X3) throw InvalidArg("unknown precision");
     const double s = norm_static_sumsq(u, p->precision == FCGLE_FP64, N, (cudaStream_t)cuda_stream);
     *out_host = std::sqrt(cell * s);
+  });
+}
+
+fcgle_status fcgle_selftest_bounded_wait(void* cuda_stream, int* code_out) {
+  return guarded([&] {
+    if (!code_out) throw InvalidArg("code_out is NULL");
+    *code_out = 0;
+    const int code = bounded_wait_selftest((cudaStream_t)cuda_stream);
+    *code_out = code;
+    if (code) throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
   });
 }
 

@@ -41,7 +41,7 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
-           "fcgle_batch_destroy", "fcgle_norm_static"]
+           "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -89,6 +89,7 @@ def _load():
         "fcgle_batch_launch_count": [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         "fcgle_batch_destroy": [H],
         "fcgle_norm_static": [ctypes.POINTER(fcgle_params), P, P, ctypes.POINTER(D)],
+        "fcgle_selftest_bounded_wait": [P, ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -245,6 +246,15 @@ def fcgle_norm_static(params, u, stream=None):
     st = ctypes.c_void_p(0) if (stream is None and isinstance(u, int)) else _stream(stream)
     _check(_lib.fcgle_norm_static(ctypes.byref(params), ptr, st, ctypes.byref(out)))
     return out.value
+
+
+def fcgle_selftest_bounded_wait(stream=None):
+    """Runs the bounded-wait self-test; returns (status, code).  The expected
+    outcome is (FCGLE_ERR_TIMEOUT, 99): the wait gave up at its limit and
+    reported it, and the context still ran the follow-up kernel."""
+    code = ctypes.c_int(-1)
+    status = _lib.fcgle_selftest_bounded_wait(_stream(stream), ctypes.byref(code))
+    return status, code.value
 
 
 def fcgle_sync(h):

@@ -63,6 +63,7 @@ def test_setup_rejects_invalid_parameters(binding, bad):
 
 def test_null_handle_rejected(binding):
     assert binding._lib.fcgle_step(None, 0, 0.1, 0.0, None) == binding.FCGLE_ERR_INVALID_ARG
+    assert binding._lib.fcgle_selftest_bounded_wait(None, None) == binding.FCGLE_ERR_INVALID_ARG
     assert binding._lib.fcgle_destroy(None) == binding.FCGLE_OK
 
 
