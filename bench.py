@@ -35,6 +35,14 @@ PARS = dict(nu=1.0, eta=0.5, gamma=1.0, kappa=1.0, zeta=0.5)
 TAU = 1e-3
 KROGSTAD_BYTES_PER_ELEM = 16 * 16 + 32 + 3 * 24 + 32 + 40 + 40 + 24   # 496 B per complex element
 
+# 2D 1023 x 1024 workload (linearly-implicit Euler and ETD2RK, 500 steps): the
+# mode products contract p = 1024, so they are bound by the tensor pipe, not HBM
+C2_NS = [1023, 1024]
+C2_BOXES = [(-20.0, 20.0)] * 2
+C2_ALPHAS = [1.3, 1.7]
+C2_PARS = dict(nu=1.0, eta=1.0, gamma=0.5, kappa=1.0, zeta=-1.0)
+C2_STEPS = 500
+
 
 def etd2rk_bytes_per_elem(d):
     """Algorithmic bytes per complex element of one split-BF16 ETD2RK step in d
@@ -129,6 +137,35 @@ def cpu_sample_batched(ninst, max_steps, budget_s):
             "cores": os.cpu_count()}
 
 
+def cpu_sample_2d(scheme, max_steps, budget_s):
+    """The FP64 oracle (as it stands) on the 2D 1023 x 1024 workload: setup,
+    then whole steps of `scheme` until max_steps or the time budget is used."""
+    from oracle import schemes, tensor
+    from paper_2510_21394_gb300 import inputs
+    t0 = time.perf_counter()
+    P = tensor.Problem(C2_NS, C2_BOXES, C2_ALPHAS, *C2_PARS.values())
+    S = tensor.Spectral(P)
+    if scheme == "lie":
+        S.F("inv", 0, TAU)
+    else:
+        S.F("phi", 1, TAU)
+        S.F("phi", 2, TAU)
+    setup = time.perf_counter() - t0
+    u = inputs.sech_pulse_noise(C2_NS, C2_BOXES, seed=0)
+    g = schemes.Nonlinearity(P)
+    done, t_run = 0, 0.0
+    while done < max_steps:
+        t1 = time.perf_counter()
+        u = schemes.integrate(S, g, scheme, TAU, 1, u, t0=done * TAU)
+        t_run += time.perf_counter() - t1
+        done += 1
+        if t_run > budget_s:
+            break
+    assert np.all(np.isfinite(u))
+    return {"value": int(np.prod(C2_NS)) * done / t_run, "seconds": t_run, "steps": done, "setup_s": setup,
+            "cores": os.cpu_count()}
+
+
 def run_cpu_sample_subprocess(n, max_steps, budget_s, timeout_s, batched=False):
     if batched:
         cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-batched", str(n), str(max_steps),
@@ -139,6 +176,15 @@ def run_cpu_sample_subprocess(n, max_steps, budget_s, timeout_s, batched=False):
                 return json.loads(line)
         raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n), str(max_steps), str(budget_s)]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError(f"cpu sample failed: {r.stderr[-2000:]}")
+
+
+def run_cpu_sample_2d_subprocess(scheme, max_steps, budget_s, timeout_s):
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-2d", scheme, str(max_steps), str(budget_s)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
     for line in r.stdout.splitlines()[::-1]:
         if line.startswith("{"):
@@ -201,6 +247,42 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense bf16 tensor peak in TFLOP/s (burst, sustained) and its provenance."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
+    return 1900.0, 1700.0, "fallback"
+
+
+def l2_flush_buffer(torch):
+    """A 256 MB device buffer; writing it evicts every line of the 129 MB L2."""
+    return torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+
+def dgemm_peak_tflops(torch, n=4096, reps=5):
+    """FP64 matrix-multiply rate of this GPU, measured here: torch.matmul on
+    n x n float64 operands (cuBLAS DGEMM), best of reps, CUDA events."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
 def kernel_source_sha():
@@ -423,6 +505,190 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_config2(args, rank, world, local_rank):
+    """2D 1023 x 1024 on (-20,20)^2, alpha = (1.3, 1.7), sech pulse + noise (seed 0),
+    linearly-implicit Euler and ETD2RK, tau = 1e-3, 500 steps, split-BF16.  Here
+    every mode product contracts p = 1024 (arithmetic intensity 256 FLOP/B at
+    complex64, x 3 for the split passes), so the roofline is the tensor pipe."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        import __graft_entry__ as g
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2510_21394_gb300 import fcgle, inputs
+    steps = args.steps if args.steps is not None else C2_STEPS
+    stream = torch.cuda.current_stream()
+    dof = int(np.prod(C2_NS))
+    u0_np = inputs.sech_pulse_noise(C2_NS, C2_BOXES, seed=0)
+    u0 = torch.from_numpy(u0_np).to(torch.complex64).cuda()
+    out = torch.empty_like(u0)
+    solver = fcgle.Solver(C2_NS, C2_BOXES, C2_ALPHAS, **C2_PARS, precision="bf16x3")
+    flush = l2_flush_buffer(torch)
+    per = {}
+    clocks = None
+    for scheme in ("lie", "etd2rk"):
+        solver.integrate(scheme, TAU, args.warmup, u0, out=out)
+        solver.sync()
+        clock = ClockSampler(gpu_index_for(local_rank)) if (rank == 0 and scheme == "etd2rk") else None
+        time.sleep(0.3 if clock else 0.0)
+        flush.fill_(1.0)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = solver.launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.integrate(scheme, TAU, steps, u0, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
+        solver.sync()
+        if clock:
+            clocks = clock.stop()
+        per[scheme] = {"value": aggregate_rate(dof, steps, ms / 1e3, world), "unit": UNIT,
+                       "ms_per_step": ms / steps, "gpu_launches": solver.launches() - l0}
+
+    # ---- dominant kernel: one split-BF16 mode product contracting p = 1024, per launch,
+    # L2 flushed before each launch, CUDA events on the launching stream
+    P = fcgle.fcgle_internal_elems(solver.h)
+    X = torch.randn(2 * P, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+    X = torch.cat([X, torch.zeros_like(X)])
+    Y = torch.empty_like(X)
+    for d_ in range(2):
+        fcgle.fcgle_mode_product(solver.h, d_, 3, X, Y)
+    torch.cuda.synchronize()
+    times = []
+    for rep in range(10):
+        for d_ in range(2):
+            flush.fill_(float(rep))
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            fcgle.fcgle_mode_product(solver.h, d_, 3, X, Y)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            times.append(k0.elapsed_time(k1))
+    solver.sync()
+    mp_ms = sum(times) / len(times)
+    p = 1024                                   # both directions pad to 1024
+    mp_flop = 3 * 2 * p * (2 * P)              # 3 split passes x 2 p flop per real output element
+    peak, peak_sus, peak_kind = measured_bf16_peak()
+    achieved = mp_flop / (mp_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "mp_b3_plain_kernel (one 1024 x 1024 mode product, p = 1024, split in/out)",
+                "peak_kind": f"{peak_kind} bf16_tflops (burst)", "launch_ms": round(mp_ms, 5),
+                "algorithmic_flop": mp_flop,
+                "flop_note": "3 bf16 passes (hi.hi + hi.lo + lo.hi) x 2 p FLOP per real output element"}
+    del X, Y
+    # whole ETD2RK step against the tensor peak (sustained): 4 Tucker operators x 2 mode products
+    step_flop = 4 * 2 * mp_flop
+    step_tf = step_flop / (per["etd2rk"]["ms_per_step"] / 1e3) / 1e12
+    step_roof = {"algorithmic_flop": step_flop, "achieved": round(step_tf, 1), "peak": peak_sus,
+                 "unit": "TFLOP/s", "frac": round(step_tf / peak_sus, 4),
+                 "peak_kind": f"{peak_kind} bf16_tflops_sustained"}
+
+    # ---- end to end through the C ABI with host buffers (ETD2RK)
+    hin = torch.from_numpy(u0_np.astype(np.complex64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    solver.integrate_host("etd2rk", TAU, steps, hin, hout)
+    e2e_s = max_over_ranks(time.perf_counter() - t1, world)
+    e2e = {"value": aggregate_rate(dof, steps, e2e_s, world), "unit": UNIT,
+           "h2d_bytes_per_step": hin.numel() * 8 / steps, "d2h_bytes_per_step": hout.numel() * 8 / steps,
+           "note": "fcgle_integrate_host: one H2D of u0 (pinned) and one D2H of u(T) per call of K steps, "
+                   "synchronised, wall clock"}
+
+    extra = {}
+    if not args.no_fp64 and rank == 0:
+        # ---- the plain FP64 GPU form: rate, its mode product against the measured DGEMM rate,
+        # and the split-BF16 error at T against it
+        dpeak = dgemm_peak_tflops(torch)
+        s64 = fcgle.Solver(C2_NS, C2_BOXES, C2_ALPHAS, **C2_PARS, precision="fp64")
+        v64 = torch.from_numpy(u0_np).cuda()
+        o64 = torch.empty_like(v64)
+        f64 = {}
+        acc_steps = min(steps, args.accuracy_steps if args.accuracy_steps is not None else steps)
+        for scheme in ("lie", "etd2rk"):
+            s64.integrate(scheme, TAU, 1, v64, out=o64)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            s64.integrate(scheme, TAU, 5, v64, out=o64)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = f0.elapsed_time(f1) / 5
+            s64.integrate(scheme, TAU, acc_steps, v64, out=o64)
+            solver.integrate(scheme, TAU, acc_steps, u0, out=out)
+            torch.cuda.synchronize()
+            d = out.to(torch.complex128) - o64
+            f64[scheme] = {"value": dof / (ms64 / 1e3), "ms_per_step": round(ms64, 3),
+                           "speedup_of_bf16x3": round(per[scheme]["value"] / world / (dof / (ms64 / 1e3)), 1),
+                           "rel_err_at_T": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(o64)),
+                           "max_rel_err_at_T": float(d.abs().max() / o64.abs().max()),
+                           "T_steps": acc_steps}
+        P64 = fcgle.fcgle_internal_elems(s64.h)
+        X64 = torch.randn(2 * P64, device="cuda", dtype=torch.float64)
+        Y64 = torch.empty_like(X64)
+        fcgle.fcgle_mode_product(s64.h, 0, 1, X64, Y64)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(3):
+            fcgle.fcgle_mode_product(s64.h, 0, 1, X64, Y64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms_mp64 = g0.elapsed_time(g1) / 3
+        p64 = 1024
+        tf64 = 2 * p64 * (2 * P64) / (ms_mp64 / 1e3) / 1e12
+        s64.sync()
+        s64.close()
+        del X64, Y64
+        extra["fp64_gpu"] = f64
+        extra["fp64_roofline"] = {"bound": "fp64", "achieved": round(tf64, 3), "peak": round(dpeak, 3),
+                                  "unit": "TFLOP/s", "frac": round(tf64 / dpeak, 4),
+                                  "kernel": "mp_simt_kernel<double> (one 1024 x 1024 mode product)",
+                                  "peak_kind": "measured here: cuBLAS DGEMM (torch.matmul float64, 4096^3, best of 5)"}
+    solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = run_cpu_sample_2d_subprocess("etd2rk", steps, 20.0, timeout_s=900)
+            cpu = {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                   "sample": f"{res['steps']} ETD2RK steps of the 1023 x 1024 workload ({res['seconds']:.1f} s), "
+                             f"numpy FP64 tensor-form oracle on the host cores, setup ({res['setup_s']:.1f} s) "
+                             f"excluded"}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": per["etd2rk"]["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": per["etd2rk"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+                "config": {"workload": "2D FCGLE 1023x1024 on (-20,20)^2, alpha=(1.3,1.7), nu=1, eta=1, gamma=0.5, "
+                                       "kappa=1, zeta=-1, no source; u0 = sech(|x|) exp(0.5 i x_1) + U(-1e-3,1e-3) "
+                                       "noise (seed 0); ETD2RK (value) and linearly-implicit Euler, tau=1e-3",
+                           "grid": C2_NS, "scheme": "etd2rk", "tau": TAU, "precision": "bf16x3",
+                           "storage": "complex64",
+                           "l2": "the workload's own working set (about 70 MB) fits in L2; L2 flushed before the "
+                                 "timed call and before each timed kernel launch",
+                           "parallelism": "replicas (one independent instance per GPU)"},
+                "schemes": per, "roofline": roofline, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": per["etd2rk"]["gpu_launches"], "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line))
+    return 0
+
+
 def batched_config(specs, use_graph):
     n2 = [sp["ns"][0] for sp in specs if len(sp["ns"]) == 2]
     n3 = [sp["ns"][0] for sp in specs if len(sp["ns"]) == 3]
@@ -606,7 +872,12 @@ def run_mp_only(args):
     g.build()
     from paper_2510_21394_gb300 import fcgle
     n = args.n
-    s = fcgle.Solver([n] * 3, BOXES, ALPHAS, **PARS, precision=args.precision)
+    if args.workload == "config2":
+        s = fcgle.Solver(C2_NS, C2_BOXES, C2_ALPHAS, **C2_PARS, precision=args.precision)
+        dims = 2
+    else:
+        s = fcgle.Solver([n] * 3, BOXES, ALPHAS, **PARS, precision=args.precision)
+        dims = 3
     P = fcgle.fcgle_internal_elems(s.h)
     if args.precision == "bf16x3":
         X = torch.randn(4 * P, device="cuda", dtype=torch.float32).to(torch.bfloat16)
@@ -616,43 +887,57 @@ def run_mp_only(args):
         flags = 1
     Y = torch.empty_like(X)
     for _ in range(args.mp_only):
-        for d_ in range(3):
+        for d_ in range(dims):
             fcgle.fcgle_mode_product(s.h, d_, flags, X, Y)
     torch.cuda.synchronize()
     s.sync()
     s.close()
-    print(json.dumps({"mp_only": args.mp_only, "n": n, "precision": args.precision, "ok": True}))
+    print(json.dumps({"mp_only": args.mp_only, "workload": args.workload, "n": n, "precision": args.precision,
+                      "ok": True}))
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for the cube workload, 500 for config2)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
-    ap.add_argument("--accuracy-steps", type=int, default=20)
+    ap.add_argument("--accuracy-steps", type=int, default=None,
+                    help="steps of the split-BF16 vs FP64 comparison (default: 20 for the cube, all for config2)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", nargs=3, default=None)
     ap.add_argument("--cpu-sample-batched", nargs=3, default=None)
+    ap.add_argument("--cpu-sample-2d", nargs=3, default=None)
     ap.add_argument("--mp-only", type=int, default=0, metavar="REPS",
                     help="only run REPS x 3 raw mode products (all directions) of the n^3 workload (profiling)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--scheme", default="krogstad", choices=sorted(SCHEME_NAMES),
                     help="cube workload: time-stepping scheme (default krogstad, the benchmark)")
     ap.add_argument("--tau", type=float, default=TAU)
-    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "adjoint"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "adjoint", "config2"],
                     help="cube: one 3D n^3 instance (default Krogstad); batched: 96 uneven ETD2RK instances; "
-                         "adjoint: gradient of a final-time misfit, 128^3 Lawson-RK2")
+                         "adjoint: gradient of a final-time misfit, 128^3 Lawson-RK2; config2: 2D 1023x1024 LIE "
+                         "and ETD2RK (tensor-pipe bound)")
     args = ap.parse_args()
+    if args.workload != "config2":
+        if args.steps is None:
+            args.steps = 200
+        if args.accuracy_steps is None:
+            args.accuracy_steps = 20
     if args.mp_only:
         return run_mp_only(args)
     if args.cpu_sample_batched:
         k, steps, budget = int(args.cpu_sample_batched[0]), int(args.cpu_sample_batched[1]), \
             float(args.cpu_sample_batched[2])
         print(json.dumps(cpu_sample_batched(k, steps, budget)))
+        return 0
+    if args.cpu_sample_2d:
+        print(json.dumps(cpu_sample_2d(args.cpu_sample_2d[0], int(args.cpu_sample_2d[1]),
+                                       float(args.cpu_sample_2d[2]))))
         return 0
     if args.cpu_sample:
         n, steps, budget = int(args.cpu_sample[0]), int(args.cpu_sample[1]), float(args.cpu_sample[2])
@@ -673,6 +958,8 @@ def main():
             return run_batched(args, rank, world, local_rank)
         if args.workload == "adjoint":
             return run_adjoint(args, rank, world, local_rank)
+        if args.workload == "config2":
+            return run_config2(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

@@ -35,6 +35,15 @@
  *   plainly instead (same kernels, bitwise the same results).
  * Errors.  Every function returns an fcgle_status; nothing throws across the
  *   ABI.  On error, fcgle_last_error() returns a thread-local message.
+ *   Failures that happen on the device while asynchronous work runs are kept
+ *   in the handle's device error word and reported by the next call that
+ *   synchronises (fcgle_sync, the _host entry points, fcgle_adjoint):
+ *   FCGLE_ERR_TIMEOUT when a bounded wait inside a tensor-core kernel gave up,
+ *   FCGLE_ERR_NUMERIC when a result tensor (the state written by fcgle_step,
+ *   fcgle_integrate and fcgle_batch_integrate, the output of fcgle_apply_f,
+ *   the gradient of fcgle_adjoint) holds a NaN or an Inf.  The check runs in
+ *   the kernel that writes the result in the user layout (no extra pass); the
+ *   result is still written.
  *   Invalid parameters (d not in 1..3, n_mu < 1, alpha_mu not in (1,2),
  *   nu <= 0, kappa <= 0, b_mu <= a_mu, fd_order not in {2,4}, unknown enum
  *   values, null pointers) give FCGLE_ERR_INVALID_ARG and leave the handle
@@ -59,7 +68,7 @@ typedef enum {
   FCGLE_ERR_INVALID_ARG = 1,
   FCGLE_ERR_NOMEM = 2,
   FCGLE_ERR_CUDA = 3,
-  FCGLE_ERR_NUMERIC = 4,     /* eigendecomposition residual too large, non-finite state */
+  FCGLE_ERR_NUMERIC = 4,     /* eigendecomposition residual too large; non-finite result state */
   FCGLE_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
   FCGLE_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
 } fcgle_status;
@@ -68,8 +77,13 @@ typedef enum {
  * mode products.  FCGLE_BF16X3: complex64 tensors (FP32 storage), mode
  * products on the tcgen05 tensor cores with each FP32 operand split as
  * hi + lo (two bf16) and hi*hi + hi*lo + lo*hi accumulated in FP32; the
- * eigendecomposition and the phi/exp scalars stay FP64. */
-typedef enum { FCGLE_FP64 = 0, FCGLE_BF16X3 = 2 } fcgle_precision;
+ * eigendecomposition is FP64 and the spectral scalars f(theta lam) are
+ * formed from FP64 coefficients and evaluated in FP32.
+ * FCGLE_TF32 (one-pass TF32 mode products) is not built: fcgle_setup returns
+ * FCGLE_ERR_UNSUPPORTED for it.  It would read the same operand bytes as
+ * FCGLE_BF16X3 (FP32 storage) at about 1e-3 relative error per mode product
+ * (10-bit mantissa) instead of about 1e-5. */
+typedef enum { FCGLE_FP64 = 0, FCGLE_TF32 = 1, FCGLE_BF16X3 = 2 } fcgle_precision;
 
 /* f in f(theta K): (1 - z)^{-1}, e^z, phi_k(z) (Eq. phi). */
 typedef enum { FCGLE_F_INV = 0, FCGLE_F_EXP = 1, FCGLE_F_PHI = 2 } fcgle_func;
@@ -139,6 +153,23 @@ fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, doubl
 fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta,
                            const void* v, void* out);
 
+/* The spectral scalars f(theta lam) (Sec. 3.2 after Eq. fKu_diag: the entries
+ * of diag(f(Lam_1 (+) ... (+) Lam_d)); Eq. phi for phi_k) evaluated on the
+ * device with exactly the arithmetic this handle's kernels use, for a host
+ * list of real eigenvalue sums s_j (lam_j = (nu + i eta) s_j, s_j being a sum
+ * of eigenvalues of the D_mu in the kernels):
+ *     out_host[2 j] + i out_host[2 j + 1] = f(theta (nu + i eta) s_j),
+ * f as in fcgle_apply_f (INV, EXP, PHI with k in 0..4).  FP64 handles evaluate
+ * in FP64 (power series for |z| < 1, the recurrence of Eq. phi otherwise);
+ * BF16X3 handles in FP32 as the tensor-core epilogues do: flags = 0 is the
+ * generic evaluator of fcgle_apply_f's epilogue, flags = 1 (PHI, k in 1..3)
+ * the per-launch polynomial in s along the ray theta (nu + i eta) that the
+ * scheme epilogues use.  For inspection and testing of the reduced-precision
+ * scalars; count entries, synchronises the stream, allocates two small
+ * temporary device buffers. */
+fcgle_status fcgle_spectral_scalars(fcgle_handle h, int func, int k, double theta, int count, const double* s_host,
+                                    double* out_host, int flags);
+
 /* One step of a one-step scheme (every scheme except LBDF2), in place:
  * u <- step(t, u) with step size tau > 0. */
 fcgle_status fcgle_step(fcgle_handle h, int scheme, double tau, double t, void* u);
@@ -162,8 +193,9 @@ fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int ns
  * States are checkpointed every ckpt_every steps (0: one segment) and each
  * segment is recomputed once, so the cost is about three forward runs and
  * the extra device memory (5 ckpt_every + nsteps / ckpt_every + 9) tensors.
- * Synchronises the stream.  The exponential is applied in the Tucker form
- * (Eq. fKu_diag with f = exp). */
+ * Synchronises the stream and reports device-side failures as fcgle_sync does;
+ * a non-finite loss or parameter gradient gives FCGLE_ERR_NUMERIC.  The
+ * exponential is applied in the Tucker form (Eq. fKu_diag with f = exp). */
 fcgle_status fcgle_adjoint(fcgle_handle h, int scheme, double tau, int nsteps, double t0, const void* u0,
                            const void* u_target, int ckpt_every, void* grad_u0, double* grad_params,
                            double* loss);
@@ -209,8 +241,10 @@ fcgle_status fcgle_norm_static(const fcgle_params* p, const void* u, void* cuda_
 
 /* Synchronises the handle's stream and reports device-side failures of the
  * work enqueued so far: FCGLE_ERR_TIMEOUT if a bounded wait inside a
- * tensor-core kernel gave up (its output is then invalid), FCGLE_ERR_CUDA on
- * an asynchronous CUDA error. */
+ * tensor-core kernel gave up (its output is then invalid), FCGLE_ERR_NUMERIC
+ * if a result tensor held a NaN or an Inf, FCGLE_ERR_CUDA on an asynchronous
+ * CUDA error.  The first failure recorded since the last report wins; the
+ * word is cleared when it is reported. */
 fcgle_status fcgle_sync(fcgle_handle h);
 
 /* Self-test of the bounded device-side waits (a library facility, not a step
@@ -288,9 +322,13 @@ fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h);
  * persistent launch over a device table of all instances' tensor maps, sizes
  * and epilogue parameters, so a step of the batch is a few launches whatever
  * the number of instances; the phases are captured into a graph per
- * (scheme, tau).  Grouped needs BF16X3 instances with d >= 2 and falls back to
- * 1 otherwise; a device-side timeout inside a grouped launch is reported on
- * instance 0's handle.  Steps with a source term run with direct launches. */
+ * (scheme, tau) and rebuilt when fcgle_set_coefficients or fcgle_set_source
+ * changed an instance since the capture.  Grouped needs BF16X3 instances with
+ * d >= 2 and falls back to 1 otherwise.  Steps with a source term run with
+ * direct launches.  The call is asynchronous and reports no device-side
+ * failure itself: call fcgle_sync on the instance handles to collect them (a
+ * timeout inside a grouped launch is recorded on instance 0's handle, a
+ * non-finite result on the instance's own handle). */
 fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,
                                    const void* const* u0, void* const* uT, int use_graph);
 

@@ -19,6 +19,9 @@ struct fcgle_ctx {
   fcgle_params prm;
   cudaStream_t stream = nullptr;
   std::unique_ptr<fcgle::EngineBase> eng;
+  // bumped by fcgle_set_coefficients / fcgle_set_source: captured batch steps
+  // carry the coefficients by value and must be rebuilt after a change
+  unsigned long long gen = 0;
 };
 
 // Batch of independent instances: one stream per group of instances (longest
@@ -50,6 +53,7 @@ struct fcgle_batch_ctx {
   };
   std::map<std::pair<int, uint64_t>, Plan> plans;
   long long grouped_kernels = 0;
+  unsigned long long gen_built = 0;   // sum of the instances' gen when graphs / plans were built
 };
 
 namespace fcgle {
@@ -105,6 +109,7 @@ void validate(const fcgle_params* p) {
   if (!std::isfinite(p->eta) || !std::isfinite(p->gamma) || !std::isfinite(p->zeta))
     throw InvalidArg("eta, gamma, zeta must be finite");
   if (p->fd_order != 2 && p->fd_order != 4) throw InvalidArg("fd_order must be 2 or 4");
+  if (p->precision == FCGLE_TF32) throw Unsupported("FCGLE_TF32 (one-pass TF32 mode products) is not built");
   if (p->precision != FCGLE_FP64 && p->precision != FCGLE_BF16X3) throw InvalidArg("unknown precision");
 }
 
@@ -118,6 +123,12 @@ void check_scheme(int scheme) {
 
 void check_tau(double tau) {
   if (!(tau > 0.0) || !std::isfinite(tau)) throw InvalidArg("tau must be positive and finite");
+}
+
+// Turns a code read from an engine's device error word into the C status.
+void report_device(int code) {
+  if (code == kErrNonFinite) throw NumericError("the result state holds a non-finite value (NaN or Inf)");
+  if (code) throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
 }
 
 }  // namespace
@@ -164,6 +175,7 @@ fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_re
         throw InvalidArg("sigma must be finite");
     }
     h->eng->set_source(nterms, sigma_reim, S_dev);
+    ++h->gen;
   });
 }
 
@@ -181,6 +193,7 @@ fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, doubl
     h->prm.gamma = gamma;
     h->prm.kappa = kappa;
     h->prm.zeta = zeta;
+    ++h->gen;
   });
 }
 
@@ -192,6 +205,23 @@ fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta, const 
     if (!std::isfinite(theta)) throw InvalidArg("theta must be finite");
     if (!v || !out) throw InvalidArg("tensor pointer is NULL");
     h->eng->apply_f(func, k, theta, v, out);
+  });
+}
+
+fcgle_status fcgle_spectral_scalars(fcgle_handle h, int func, int k, double theta, int count, const double* s_host,
+                                    double* out_host, int flags) {
+  return guarded([&] {
+    check_handle(h);
+    if (func < FCGLE_F_INV || func > FCGLE_F_PHI) throw InvalidArg("unknown func");
+    if (func == FCGLE_F_PHI && (k < 0 || k > 4)) throw InvalidArg("phi order k must be in 0..4");
+    if (!std::isfinite(theta)) throw InvalidArg("theta must be finite");
+    if (count < 0) throw InvalidArg("count must be >= 0");
+    if (count > 0 && (!s_host || !out_host)) throw InvalidArg("pointer is NULL");
+    for (int j = 0; j < count; ++j)
+      if (!std::isfinite(s_host[j])) throw InvalidArg("eigenvalue sums must be finite");
+    if (flags & ~1) throw InvalidArg("unknown flags");
+    if ((flags & 1) && h->prm.precision != FCGLE_BF16X3) throw InvalidArg("the ray form needs a BF16X3 handle");
+    h->eng->spectral_scalars(func, k, theta, count, s_host, out_host, flags);
   });
 }
 
@@ -227,8 +257,7 @@ fcgle_status fcgle_integrate_host(fcgle_handle h, int scheme, double tau, int ns
     if (nsteps < 0) throw InvalidArg("nsteps must be >= 0");
     if (!u0_host || !uT_host) throw InvalidArg("tensor pointer is NULL");
     h->eng->integrate_host(scheme, tau, nsteps, t0, u0_host, uT_host);
-    if (int code = h->eng->device_error())
-      throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
+    report_device(h->eng->device_error());
   });
 }
 
@@ -242,6 +271,10 @@ fcgle_status fcgle_adjoint(fcgle_handle h, int scheme, double tau, int nsteps, d
     if (ckpt_every < 0) throw InvalidArg("ckpt_every must be >= 0");
     if (!u0 || !u_target || !grad_u0 || !grad_params || !loss) throw InvalidArg("pointer is NULL");
     h->eng->adjoint(scheme, tau, nsteps, t0, u0, u_target, ckpt_every, grad_u0, grad_params, loss);
+    report_device(h->eng->device_error());
+    if (!std::isfinite(*loss)) throw NumericError("the misfit is not finite");
+    for (int k = 0; k < 5; ++k)
+      if (!std::isfinite(grad_params[k])) throw NumericError("a parameter gradient is not finite");
   });
 }
 
@@ -284,8 +317,7 @@ fcgle_status fcgle_selftest_bounded_wait(void* cuda_stream, int* code_out) {
 fcgle_status fcgle_sync(fcgle_handle h) {
   return guarded([&] {
     check_handle(h);
-    if (int code = h->eng->device_error())
-      throw DeviceTimeout("a bounded device-side wait gave up (code " + std::to_string(code) + ")");
+    report_device(h->eng->device_error());
   });
 }
 
@@ -333,14 +365,22 @@ fcgle_status fcgle_destroy(fcgle_handle h) {
 }
 
 // ------------------------------------------------------------------ batches
-static void batch_free(fcgle_batch_ctx* b) {
-  if (!b) return;
+// Drops every captured step graph and grouped plan (after the work that may
+// still use them has finished).
+static void batch_drop_cache(fcgle_batch_ctx* b) {
   if (b->origin) cudaStreamSynchronize(b->origin);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : b->plans) {
     if (kv.second.graph) cudaGraphExecDestroy(kv.second.graph);
     if (kv.second.dev) cudaFree(kv.second.dev);
   }
+  b->graphs.clear();
+  b->plans.clear();
+}
+
+static void batch_free(fcgle_batch_ctx* b) {
+  if (!b) return;
+  batch_drop_cache(b);
   for (auto* h : b->inst) delete h;
   for (auto st : b->streams) {
     cudaStreamSynchronize(st);
@@ -521,6 +561,13 @@ fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int ns
     const int n = (int)b->inst.size(), ns = (int)b->streams.size();
     for (int i = 0; i < n; ++i)
       if (!u0[i] || !uT[i]) throw InvalidArg("tensor pointer is NULL");
+    // captured steps hold the coefficients and sources they were built with
+    unsigned long long gen = 0;
+    for (auto* h : b->inst) gen += h->gen;
+    if (gen != b->gen_built) {
+      batch_drop_cache(b);
+      b->gen_built = gen;
+    }
     // the caller's stream may be the legacy default stream, which cannot be
     // captured: all work is ordered through the internal origin stream
     auto fork = [&] {

@@ -24,6 +24,9 @@ namespace fcgle {
 
 constexpr int kMaxDim = 3;
 constexpr int kMaxSrc = 4;
+// Device error word codes: 1..99 name the bounded wait that gave up (a
+// timeout); kErrNonFinite marks a NaN or Inf found in a result state.
+constexpr int kErrNonFinite = 100;
 
 struct Shape {
   int d = 0;
@@ -58,8 +61,10 @@ void throw_cuda(cudaError_t e, const char* where);
 // vec order) and the internal planar padded layout.
 template <typename T>
 void pack(const Shape& s, const T* user, T* internal, cudaStream_t st, long long& nl);
+// With `nonfinite` set, a NaN or Inf among the unpacked values records
+// kErrNonFinite in that device error word (unless it already holds a code).
 template <typename T>
-void unpack(const Shape& s, const T* internal, T* user, cudaStream_t st, long long& nl);
+void unpack(const Shape& s, const T* internal, T* user, cudaStream_t st, long long& nl, int* nonfinite = nullptr);
 
 // g(t, u) = gamma u - (kappa + i zeta)|u|^2 u + sum_k exp(sigma_k t) S_k.
 struct GParams {
@@ -104,6 +109,11 @@ void spec_combo(const Shape& s, const LamVecs& lv, const SpecArgs<T>& a, cudaStr
 template <typename T>
 void fill_F(const Shape& s, const LamVecs& lv, int func, int ell, double theta, T* F,
             cudaStream_t st, long long& nl);
+
+// The same FP64 evaluation on a device list of real eigenvalue sums s_j:
+// out[2 j] + i out[2 j + 1] = f(theta (c_re + i c_im) s_j).
+void spectral_scalars_f64(int n, const double* s_dev, double c_re, double c_im, int func, int ell, double theta,
+                          double* out_dev, cudaStream_t st, long long& nl);
 
 // Exact flow of w' = gamma w - (kappa + i zeta)|w|^2 w over time t (Sec. 4).
 template <typename T>

@@ -192,6 +192,18 @@ class Engine : public EngineBase {
     ecache_.clear();
   }
 
+  void spectral_scalars(int func, int k, double theta, int count, const double* s_host, double* out_host,
+                        int) override {
+    if (count <= 0) return;
+    DevBuf<double> sd((size_t)count), od(2 * (size_t)count);
+    FCGLE_CUDA(cudaMemcpyAsync(sd.ptr, s_host, (size_t)count * 8, cudaMemcpyHostToDevice, st_));
+    const int f = (func == FCGLE_F_PHI && k == 0) ? FCGLE_F_EXP : func;
+    spectral_scalars_f64(count, sd.ptr, prm_.nu, prm_.eta, f == FCGLE_F_INV ? 0 : (f == FCGLE_F_EXP ? 1 : 2), k,
+                         theta, od.ptr, st_, launches);
+    FCGLE_CUDA(cudaMemcpyAsync(out_host, od.ptr, 2 * (size_t)count * 8, cudaMemcpyDeviceToHost, st_));
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+  }
+
   int device_error() override {
     int h = 0;
     FCGLE_CUDA(cudaStreamSynchronize(st_));
@@ -212,7 +224,7 @@ class Engine : public EngineBase {
       scale(F(func, k, theta), Xh, Xh);
       tucker(Xh, X, false);
     }
-    unpack<T>(s_, X, (T*)out, st_, launches);
+    unpack<T>(s_, X, (T*)out, st_, launches, err_->ptr);
   }
 
   // ---------------------------------------------------------- schemes
@@ -222,14 +234,14 @@ class Engine : public EngineBase {
     prepare(scheme, tau);
     if (needs_uhat(scheme)) tucker(U, B(kUh), true);
     one_step(scheme, tau, t);
-    unpack<T>(s_, U, (T*)u, st_, launches);
+    unpack<T>(s_, U, (T*)u, st_, launches, err_->ptr);
   }
 
   void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
     T* U = B(kU);
     pack<T>(s_, (const T*)u0, U, st_, launches);
     run(scheme, tau, nsteps, t0);
-    unpack<T>(s_, B(kU), (T*)uT, st_, launches);
+    unpack<T>(s_, B(kU), (T*)uT, st_, launches, err_->ptr);
   }
 
   void begin_steps(int scheme, double tau, double t0, const void* u0) override {
@@ -253,7 +265,7 @@ class Engine : public EngineBase {
       one_step(rs_scheme_, rs_tau_, t);
     }
   }
-  void end_steps(void* uT) override { unpack<T>(s_, B(kU), (T*)uT, st_, launches); }
+  void end_steps(void* uT) override { unpack<T>(s_, B(kU), (T*)uT, st_, launches, err_->ptr); }
   bool time_dependent() const override { return gp_.nsrc > 0; }
 
   void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
@@ -262,7 +274,7 @@ class Engine : public EngineBase {
     FCGLE_CUDA(cudaMemcpyAsync(host_stage_->ptr, u0, bytes, cudaMemcpyHostToDevice, st_));
     pack<T>(s_, host_stage_->ptr, B(kU), st_, launches);
     run(scheme, tau, nsteps, t0);
-    unpack<T>(s_, B(kU), host_stage_->ptr, st_, launches);
+    unpack<T>(s_, B(kU), host_stage_->ptr, st_, launches, err_->ptr);
     FCGLE_CUDA(cudaMemcpyAsync(uT, host_stage_->ptr, bytes, cudaMemcpyDeviceToHost, st_));
     FCGLE_CUDA(cudaStreamSynchronize(st_));
   }
@@ -291,7 +303,7 @@ class Engine : public EngineBase {
       pack<T>(s_, (const T*)u0, U0, st_, launches);
       pack<T>(s_, (const T*)target, TG, st_, launches);
       adjoint_lawson_rk2<T>(*this, tau, nsteps, t0, U0, TG, ckpt, GR, grad_params, loss);
-      unpack<T>(s_, GR, (T*)grad_u0, st_, launches);
+      unpack<T>(s_, GR, (T*)grad_u0, st_, launches, err_->ptr);
       FCGLE_CUDA(cudaStreamSynchronize(st_));
     } catch (...) {
       release_all();

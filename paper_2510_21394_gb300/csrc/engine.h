@@ -56,6 +56,10 @@ class EngineBase {
     mode_product(mu, flags & 1, X, Y);
   }
   virtual size_t internal_elems() const = 0;
+  // f(theta lam) for lam = (nu + i eta) s_j, host lists, evaluated on the device
+  // by the arithmetic the handle's kernels use; synchronous
+  virtual void spectral_scalars(int func, int k, double theta, int count, const double* s_host, double* out_host,
+                                int flags) = 0;
   // stepping interface (batched CUDA graphs): pack u0 and build the loop's entry
   // state; enqueue step n; unpack the state.  No host synchronisation inside
   // one_step, so a step can be captured into a graph.

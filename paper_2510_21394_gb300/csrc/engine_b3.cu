@@ -189,6 +189,27 @@ __global__ void to_split_kernel(uint32_t n, const float* __restrict__ X, SplitOu
   }
 }
 
+// f(theta lam_j) with lam_j = (c_re + i c_im) s_j as the epilogues evaluate it:
+// ray == 0: fspec on z = theta lam (the apply_f epilogue); ray != 0: phi_ell
+// (ell in 1..3) by the per-launch polynomial along the ray (the scheme epilogues)
+__global__ void scalars_b3_kernel(int n, const double* __restrict__ sv, float c_re, float c_im, float theta, int kind,
+                                  int ray, b3::PhiPoly ph, int ell, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const float s = (float)sv[j];
+    float fr, fi;
+    if (ray) {
+      float pr[3], pi[3];
+      b3::phi123_s(ph, s, pr, pi);
+      fr = pr[ell - 1];
+      fi = pi[ell - 1];
+    } else {
+      b3::fspec(kind, theta * (c_re * s), theta * (c_im * s), fr, fi);
+    }
+    out[2 * j] = fr;
+    out[2 * j + 1] = fi;
+  }
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   const long long cap = (long long)num_sms() * 16;
@@ -321,6 +342,21 @@ class EngineB3 : public EngineBase {
     gs_.zeta = (float)zeta;
   }
 
+  void spectral_scalars(int func, int k, double theta, int count, const double* s_host, double* out_host,
+                        int flags) override {
+    const bool ray = flags & 1;
+    if (ray && (func != FCGLE_F_PHI || k < 1 || k > 3))
+      throw InvalidArg("the ray polynomial form evaluates phi_1..phi_3 only");
+    if (count <= 0) return;
+    DevMem<double> sd((size_t)count), od(2 * (size_t)count);
+    FCGLE_CUDA(cudaMemcpyAsync(sd.ptr, s_host, (size_t)count * 8, cudaMemcpyHostToDevice, st_));
+    scalars_b3_kernel<<<grid_for(count), 256, 0, st_>>>(count, sd.ptr, lf_.c_re, lf_.c_im, (float)theta,
+                                                       fkind(func, k), ray ? 1 : 0, phipoly(theta), k, od.ptr);
+    FCGLE_LAUNCHED(launches);
+    FCGLE_CUDA(cudaMemcpyAsync(out_host, od.ptr, 2 * (size_t)count * 8, cudaMemcpyDeviceToHost, st_));
+    FCGLE_CUDA(cudaStreamSynchronize(st_));
+  }
+
   int device_error() override {
     int h = 0;
     FCGLE_CUDA(cudaStreamSynchronize(st_));
@@ -356,20 +392,20 @@ class EngineB3 : public EngineBase {
     gsplit(X, 0.0, 1.f, 0.f, V);
     tucker(V, true, b3::EpiScaleF{P32(), lf_, fkind(func, k), (float)theta, V});
     tucker(V, false, b3::EpiStoreF32{P32(), X});
-    unpack_f32(X, (float*)out);
+    unpack_f32(X, (float*)out, true);
   }
 
   // ---------------------------------------------------------- schemes
   void step(int scheme, double tau, double t, void* u) override {
     pack_f32((const float*)u, F32(kU));
     run(scheme, tau, 1, t);
-    unpack_f32(F32(kU), (float*)u);
+    unpack_f32(F32(kU), (float*)u, true);
   }
 
   void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
     pack_f32((const float*)u0, F32(kU));
     run(scheme, tau, nsteps, t0);
-    unpack_f32(F32(kU), (float*)uT);
+    unpack_f32(F32(kU), (float*)uT, true);
   }
 
   void integrate_host(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) override {
@@ -378,7 +414,7 @@ class EngineB3 : public EngineBase {
     FCGLE_CUDA(cudaMemcpyAsync(host_stage_->ptr, u0, bytes, cudaMemcpyHostToDevice, st_));
     pack_f32(host_stage_->ptr, F32(kU));
     run(scheme, tau, nsteps, t0);
-    unpack_f32(F32(kU), host_stage_->ptr);
+    unpack_f32(F32(kU), host_stage_->ptr, true);
     FCGLE_CUDA(cudaMemcpyAsync(uT, host_stage_->ptr, bytes, cudaMemcpyDeviceToHost, st_));
     FCGLE_CUDA(cudaStreamSynchronize(st_));
   }
@@ -430,7 +466,7 @@ class EngineB3 : public EngineBase {
       pack_f32((const float*)u0, U0);
       pack_f32((const float*)target, TG);
       adjoint_lawson_rk2<float>(*this, tau, nsteps, t0, U0, TG, ckpt, GR, grad_params, loss);
-      unpack_f32(GR, (float*)grad_u0);
+      unpack_f32(GR, (float*)grad_u0, true);
       FCGLE_CUDA(cudaStreamSynchronize(st_));
     } catch (...) {
       release_all();
@@ -654,7 +690,10 @@ class EngineB3 : public EngineBase {
   }
 
   void pack_f32(const float* user, float* U) { pack<float>(s_, user, U, st_, launches); }
-  void unpack_f32(const float* U, float* user) { unpack<float>(s_, U, user, st_, launches); }
+  // check = true: a NaN or Inf among the values is recorded in the device error word
+  void unpack_f32(const float* U, float* user, bool check = false) {
+    unpack<float>(s_, U, user, st_, launches, check ? err_->ptr : nullptr);
+  }
 
   b3::GTime gtime(double t) const {
     b3::GTime g;
@@ -847,7 +886,7 @@ class EngineB3 : public EngineBase {
   void one_step(int n) override { step(n); }
   void end_steps(void* uT) override {
     finish();
-    unpack_f32(F32(kU), (float*)uT);
+    unpack_f32(F32(kU), (float*)uT, true);
   }
   bool time_dependent() const override { return gs_.nsrc > 0; }
   bool set_recorder(std::vector<GroupRec>* rec) override {

@@ -88,6 +88,18 @@ double norm_static_sumsq(const void* u, bool fp64, unsigned long long n_complex,
   int dev = 0;
   FCGLE_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) throw Unsupported("device ordinal beyond the library's table");
+  // the scratch used is the current device's: the stream and the tensor must be on it too
+  int sdev = dev;
+  if (st) FCGLE_CUDA(cudaStreamGetDevice(st, &sdev));
+  if (sdev != dev)
+    throw InvalidArg("the stream belongs to device " + std::to_string(sdev) + " but device " + std::to_string(dev) +
+                     " is current");
+  cudaPointerAttributes pa;
+  FCGLE_CUDA(cudaPointerGetAttributes(&pa, u));
+  if (pa.type == cudaMemoryTypeUnregistered) throw InvalidArg("u is not memory known to CUDA");
+  if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+    throw InvalidArg("u lives on device " + std::to_string(pa.device) + " but device " + std::to_string(dev) +
+                     " is current");
   // One scratch array per device and process: calls that overlapped on one
   // device would race on it, so the whole call (which ends with a stream
   // synchronisation) holds this lock.

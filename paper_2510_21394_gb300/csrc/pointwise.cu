@@ -85,8 +85,9 @@ __global__ void pack_kernel(Shape s, const T* __restrict__ user, T* __restrict__
 }
 
 template <typename T>
-__global__ void unpack_kernel(Shape s, const T* __restrict__ X, T* __restrict__ user) {
+__global__ void unpack_kernel(Shape s, const T* __restrict__ X, T* __restrict__ user, int* __restrict__ nonfinite) {
   const size_t N = s.N;
+  bool bad = false;
   for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < N; u += (size_t)gridDim.x * blockDim.x) {
     size_t rem = u, q = 0, stride = 1;
     for (int mu = 0; mu < s.d; ++mu) {
@@ -95,9 +96,13 @@ __global__ void unpack_kernel(Shape s, const T* __restrict__ X, T* __restrict__ 
       q += (size_t)j * stride;
       stride *= s.p[mu];
     }
-    user[2 * u] = X[q];
-    user[2 * u + 1] = X[s.P + q];
+    const T re = X[q], im = X[s.P + q];
+    user[2 * u] = re;
+    user[2 * u + 1] = im;
+    bad |= !(isfinite(re) && isfinite(im));
   }
+  // a non-finite entry is recorded unless an earlier device error is already there
+  if (bad && nonfinite) atomicCAS(nonfinite, 0, kErrNonFinite);
 }
 
 // ------------------------------------------------------------- g(t, u)
@@ -289,6 +294,34 @@ __device__ void phi_eval(int ell, double zr, double zi, double& fr, double& fi) 
   fi = pi;
 }
 
+// f(z) for func 0: 1/(1 - z), 1: e^z, 2: phi_ell (FP64)
+__device__ __forceinline__ void f_eval64(int func, int ell, double zr, double zi, double& fr, double& fi) {
+  if (func == 0) {
+    const double ar = 1.0 - zr, ai = -zi, den = ar * ar + ai * ai;
+    fr = ar / den;
+    fi = -ai / den;
+  } else if (func == 1) {
+    double sn, cs;
+    sincos(zi, &sn, &cs);
+    const double ex = exp(zr);
+    fr = ex * cs;
+    fi = ex * sn;
+  } else {
+    phi_eval(ell, zr, zi, fr, fi);
+  }
+}
+
+// out[2 j], out[2 j + 1] = f(theta (c_re + i c_im) s_j)
+__global__ void scalars_f64_kernel(int n, const double* __restrict__ sv, double c_re, double c_im, int func,
+                                   int ell, double theta, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double fr, fi;
+    f_eval64(func, ell, theta * c_re * sv[j], theta * c_im * sv[j], fr, fi);
+    out[2 * j] = fr;
+    out[2 * j + 1] = fi;
+  }
+}
+
 template <typename T>
 __global__ void fill_F_kernel(size_t P, LamDev L, Shape s, int func, int ell, double theta, T* __restrict__ F) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
@@ -302,22 +335,7 @@ __global__ void fill_F_kernel(size_t P, LamDev L, Shape s, int func, int ell, do
       sum += L.lam[mu][j];
     }
     double fr = 0.0, fi = 0.0;
-    if (valid) {
-      const double zr = theta * L.c_re * sum, zi = theta * L.c_im * sum;
-      if (func == 0) {            // 1/(1-z)
-        const double ar = 1.0 - zr, ai = -zi, den = ar * ar + ai * ai;
-        fr = ar / den;
-        fi = -ai / den;
-      } else if (func == 1) {     // e^z
-        double sn, cs;
-        sincos(zi, &sn, &cs);
-        const double ex = exp(zr);
-        fr = ex * cs;
-        fi = ex * sn;
-      } else {
-        phi_eval(ell, zr, zi, fr, fi);
-      }
-    }
+    if (valid) f_eval64(func, ell, theta * L.c_re * sum, theta * L.c_im * sum, fr, fi);
     F[q] = (T)fr;
     F[P + q] = (T)fi;
   }
@@ -381,8 +399,8 @@ void pack(const Shape& s, const T* user, T* X, cudaStream_t st, long long& nl) {
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
-void unpack(const Shape& s, const T* X, T* user, cudaStream_t st, long long& nl) {
-  unpack_kernel<T><<<grid_for(s.N, 256), 256, 0, st>>>(s, X, user);
+void unpack(const Shape& s, const T* X, T* user, cudaStream_t st, long long& nl, int* nonfinite) {
+  unpack_kernel<T><<<grid_for(s.N, 256), 256, 0, st>>>(s, X, user, nonfinite);
   FCGLE_LAUNCHED(nl);
 }
 
@@ -426,6 +444,12 @@ void spec_combo(const Shape& s, const LamVecs& lv, const SpecArgs<T>& a, cudaStr
   FCGLE_LAUNCHED(nl);
 }
 
+void spectral_scalars_f64(int n, const double* s_dev, double c_re, double c_im, int func, int ell, double theta,
+                          double* out_dev, cudaStream_t st, long long& nl) {
+  scalars_f64_kernel<<<grid_for((size_t)n, 256), 256, 0, st>>>(n, s_dev, c_re, c_im, func, ell, theta, out_dev);
+  FCGLE_LAUNCHED(nl);
+}
+
 template <typename T>
 void fill_F(const Shape& s, const LamVecs& lv, int func, int ell, double theta, T* F, cudaStream_t st,
             long long& nl) {
@@ -452,7 +476,7 @@ void sumsq(const Shape& s, const T* X, double* out_dev, cudaStream_t st, long lo
 
 #define INST(T)                                                                                           \
   template void pack<T>(const Shape&, const T*, T*, cudaStream_t, long long&);                           \
-  template void unpack<T>(const Shape&, const T*, T*, cudaStream_t, long long&);                         \
+  template void unpack<T>(const Shape&, const T*, T*, cudaStream_t, long long&, int*);                         \
   template void gcombo<T>(const Shape&, const GParams&, double, const T*, const T*, const T*, double,     \
                           double, double, double, double, double, T*, cudaStream_t, long long&);         \
   template void spec_combo<T>(const Shape&, const LamVecs&, const SpecArgs<T>&, cudaStream_t, long long&); \

@@ -25,6 +25,7 @@ FCGLE_ERR_TIMEOUT = 5
 FCGLE_ERR_UNSUPPORTED = 6
 
 FCGLE_FP64 = 0
+FCGLE_TF32 = 1      # not built: fcgle_setup answers FCGLE_ERR_UNSUPPORTED
 FCGLE_BF16X3 = 2
 
 FCGLE_F_INV = 0
@@ -41,7 +42,7 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
-           "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait"]
+           "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait", "fcgle_spectral_scalars"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -90,6 +91,7 @@ def _load():
         "fcgle_batch_destroy": [H],
         "fcgle_norm_static": [ctypes.POINTER(fcgle_params), P, P, ctypes.POINTER(D)],
         "fcgle_selftest_bounded_wait": [P, ctypes.POINTER(I)],
+        "fcgle_spectral_scalars": [H, I, I, D, I, ctypes.POINTER(D), ctypes.POINTER(D), I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -207,6 +209,18 @@ def fcgle_apply_f(h, func, k, theta, v, out):
     _check(_lib.fcgle_apply_f(h, func, int(k), float(theta), _ptr(v), _ptr(out)))
 
 
+def fcgle_spectral_scalars(h, func, k, theta, s, flags=0):
+    """f(theta (nu + i eta) s_j) for a list of real eigenvalue sums s, evaluated
+    on the device by the handle's own arithmetic; returns a list of complex."""
+    func = FUNCS[func] if isinstance(func, str) else int(func)
+    s = [float(x) for x in s]
+    n = len(s)
+    sin = (ctypes.c_double * max(1, n))(*s)
+    out = (ctypes.c_double * max(1, 2 * n))()
+    _check(_lib.fcgle_spectral_scalars(h, func, int(k), float(theta), n, sin, out, int(flags)))
+    return [complex(out[2 * j], out[2 * j + 1]) for j in range(n)]
+
+
 def fcgle_step(h, scheme, tau, t, u):
     scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     _check(_lib.fcgle_step(h, scheme, float(tau), float(t), _ptr(u)))
@@ -238,10 +252,35 @@ def fcgle_norm(h, u):
     return out.value
 
 
+def _check_norm_static_tensor(params, u):
+    """A torch tensor given to fcgle_norm_static must hold exactly the tensor
+    that params describe: complex128 for FP64, complex64 for BF16X3, prod(n)
+    entries, contiguous, on the current CUDA device (the C side trusts these)."""
+    want = torch.complex128 if params.precision == FCGLE_FP64 else torch.complex64
+    n = 1
+    for mu in range(max(0, min(3, params.d))):
+        n *= int(params.n[mu])
+    bad = None
+    if u.dtype != want:
+        bad = f"u has dtype {u.dtype}, the precision needs {want}"
+    elif u.numel() != n:
+        bad = f"u has {u.numel()} entries, params describe {n}"
+    elif not u.is_contiguous():
+        bad = "u must be contiguous"
+    elif not u.is_cuda:
+        bad = "u must be a CUDA tensor"
+    elif u.device.index != torch.cuda.current_device():
+        bad = f"u is on cuda:{u.device.index} but cuda:{torch.cuda.current_device()} is current"
+    if bad:
+        raise FcgleError(FCGLE_ERR_INVALID_ARG, bad)
+
+
 def fcgle_norm_static(params, u, stream=None):
     """Discrete L2 norm without a handle or device allocation; u is a device
-    tensor or a raw device address (int)."""
+    tensor (checked against params) or a raw device address (int)."""
     out = ctypes.c_double()
+    if not isinstance(u, int):
+        _check_norm_static_tensor(params, u)
     ptr = ctypes.c_void_p(u) if isinstance(u, int) else _ptr(u)
     st = ctypes.c_void_p(0) if (stream is None and isinstance(u, int)) else _stream(stream)
     _check(_lib.fcgle_norm_static(ctypes.byref(params), ptr, st, ctypes.byref(out)))

@@ -69,3 +69,26 @@ def test_null_handle_rejected(binding):
 
 class _FakeStream:
     cuda_stream = 0
+
+
+def test_tf32_precision_is_reported_unsupported(binding):
+    with pytest.raises(binding.FcgleError) as e:
+        binding.fcgle_setup([4, 5], [(-1.0, 1.0)] * 2, [1.5, 1.5], 1.0, 0.0, 0.0, 1.0, 0.0,
+                            precision=binding.FCGLE_TF32, stream=_FakeStream())
+    assert e.value.status == binding.FCGLE_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["dtype", "numel", "contiguous", "device"])
+def test_norm_static_wrapper_rejects_mismatched_tensors(binding, case):
+    """The Python wrapper of fcgle_norm_static checks the tensor against the
+    params before the C call (which trusts them); each mismatch is rejected."""
+    torch = pytest.importorskip("torch")
+    p = binding.make_params([6, 4], [(-1.0, 1.0)] * 2, [1.5, 1.5], 1.0, 0.0, 0.0, 1.0, 0.0, precision="bf16x3")
+    u = {"dtype": torch.zeros((4, 6), dtype=torch.complex128),
+         "numel": torch.zeros((4, 5), dtype=torch.complex64),
+         "contiguous": torch.zeros((6, 4), dtype=torch.complex64).t(),
+         "device": torch.zeros((4, 6), dtype=torch.complex64)}[case]
+    with pytest.raises(binding.FcgleError) as e:
+        binding.fcgle_norm_static(p, u)
+    assert e.value.status == binding.FCGLE_ERR_INVALID_ARG
+    assert {"dtype": "dtype", "numel": "entries", "contiguous": "contiguous", "device": "CUDA"}[case] in str(e.value)
