@@ -27,5 +27,29 @@ def rand_tensor(ns, seed):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
-def rel(a, b):
+def rel_norm(a, b):
+    """Norm-wise relative error ||a - b||_2 / ||b||_2."""
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def rel_max(a, b):
+    """Max-elementwise relative error ||a - b||_inf / ||b||_inf: an error confined
+    to a few entries (a ragged tail, a padding row) is not diluted by the rest."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel(a, b):
+    """The larger of the norm-wise and the max-elementwise relative errors; every
+    parity comparison of the GPU tests holds both to its tolerance."""
+    return max(rel_norm(a, b), rel_max(a, b))
+
+
+def rel_dev(a, b):
+    """rel() for two CUDA tensors (a is promoted to b's dtype), without a host copy."""
+    import torch
+    a = a.to(b.dtype)
+    d = a - b
+    nrm = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(b))
+    mx = float(d.abs().max() / b.abs().max())
+    return max(nrm, mx)

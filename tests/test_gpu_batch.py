@@ -6,6 +6,7 @@ import pytest
 
 from oracle import schemes, tensor
 from paper_2510_21394_gb300 import inputs
+from helpers import rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -78,7 +79,7 @@ def test_batch_instance_against_oracle(fc):
         ref = schemes.integrate(tensor.Spectral(P), schemes.Nonlinearity(P), "etd2rk", 5e-3, 8,
                                 x0.astype(np.complex64).astype(np.complex128))
         got = o.cpu().numpy().astype(np.complex128)
-        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+        assert rel(got, ref) <= 1e-4
     b.close()
 
 
@@ -98,3 +99,31 @@ def test_batch_with_source_falls_back_to_direct_launches(fc):
     assert b.launches()[1] == 0            # no graph: the source makes the steps time dependent
     assert float(torch.abs(outs[0]).max()) > 0 and float(torch.abs(outs[1]).max()) == 0
     b.close()
+
+
+@pytest.mark.parametrize("graph", [True, "grouped"])
+def test_batch_replays_new_coefficients(fc, graph):
+    """A captured step holds the coefficients it was built with: after
+    fcgle_set_coefficients on one instance the batch must rebuild it, and the
+    result must equal that of a fresh batch created with the new values."""
+    specs = _specs(seed=7, n2=3, n3=2)
+    dt = torch.complex64
+    u0 = [torch.from_numpy(inputs.gaussian_pulse(sp["ns"], sp["boxes"])).to(dt).cuda() for sp in specs]
+    grouped = graph == "grouped"
+    b = fc.Batch(specs, precision="bf16x3")
+    b.integrate("etd2rk", 1e-3, 4, u0, use_graph=True, grouped=grouped)
+    sp1 = dict(specs[1])
+    sp1["gamma"] = sp1["gamma"] + 0.7
+    sp1["zeta"] = -sp1["zeta"]
+    fc.fcgle_set_coefficients(b.instance(1), sp1["nu"], sp1["eta"], sp1["gamma"], sp1["kappa"], sp1["zeta"])
+    got = b.integrate("etd2rk", 1e-3, 4, u0, use_graph=True, grouped=grouped)
+    specs2 = list(specs)
+    specs2[1] = sp1
+    b2 = fc.Batch(specs2, precision="bf16x3")
+    ref = b2.integrate("etd2rk", 1e-3, 4, u0, use_graph=True, grouped=grouped)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        fc.fcgle_sync(b.instance(i))
+        assert torch.equal(got[i], ref[i]), i
+    b.close()
+    b2.close()

@@ -56,7 +56,7 @@ def test_apply_f_parity(fc, case):
     v = _dev(V)
     V32 = V.astype(np.complex64).astype(np.complex128)
     for th in (1e-3, 0.07):
-        for func, k in (("inv", 0), ("exp", 0), ("phi", 1), ("phi", 2), ("phi", 3)):
+        for func, k in (("inv", 0), ("exp", 0), ("phi", 0), ("phi", 1), ("phi", 2), ("phi", 3), ("phi", 4)):
             ref = S.apply_f(func, k, th, V32)
             got = _host(s.apply_f(func, k, th, v))
             assert rel(got, ref) <= TOL_APPLY, (func, k, th, rel(got, ref))

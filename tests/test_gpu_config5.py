@@ -36,18 +36,30 @@ def test_config5_gradients(fc):
     loss, g64, gp64 = s64.adjoint("lawson_rk2", TAU, M, v0, target, ckpt_every=CK)
     assert loss > 0 and np.all(np.isfinite(gp64))
 
-    def J(pars):
+    def J(pars, u=v0):
         s64.set_coefficients(*pars)
-        uT = s64.integrate("lawson_rk2", TAU, M, v0)
+        uT = s64.integrate("lawson_rk2", TAU, M, u)
         s64.set_coefficients(*PARS)
         return 0.5 * float(torch.sum(torch.abs(uT - target) ** 2))
-    for k in (1, 3):   # eta (through exp(tau K)) and kappa (through g)
+    # central differences of the FP64 GPU forward map, every parameter
+    # (nu, eta through exp(tau K); gamma, kappa, zeta through g) and u0 along one
+    # seeded direction d: dJ/de J(u0 + e d) = Re <grad_u0, d> with the real-sense
+    # gradient convention.  Step 1e-5 relative: truncation ~h^2 ~ 1e-10, FP64
+    # rounding of J over the step ~1e-10 relative, both far below 1e-6.
+    for k in range(5):
         h = 1e-5 * max(1.0, abs(PARS[k]))
         pp, pm = list(PARS), list(PARS)
         pp[k] += h
         pm[k] -= h
         fd = (J(pp) - J(pm)) / (2 * h)
-        assert gp64[k] == pytest.approx(fd, rel=1e-5), (k, gp64[k], fd)
+        assert gp64[k] == pytest.approx(fd, rel=1e-6), (k, gp64[k], fd)
+    rng = np.random.default_rng(31)
+    d = torch.from_numpy(rng.standard_normal(u0.shape) + 1j * rng.standard_normal(u0.shape)).cuda()
+    d = d * (v0.abs().max() / d.abs().max())
+    h = 1e-5
+    fd = (J(PARS, v0 + h * d) - J(PARS, v0 - h * d)) / (2 * h)
+    dirder = float(torch.sum((g64.conj() * d).real))
+    assert dirder == pytest.approx(fd, rel=1e-6), (dirder, fd)
 
     s32 = fc.Solver(NS, BOXES, AL, *PARS, precision="bf16x3")
     loss32, g32, gp32 = s32.adjoint("lawson_rk2", TAU, M, v0.to(torch.complex64), target.to(torch.complex64),

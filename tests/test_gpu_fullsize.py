@@ -9,7 +9,7 @@ the reduced-precision form)."""
 import numpy as np
 import pytest
 
-from helpers import CONFIG2, CONFIG3, rel
+from helpers import CONFIG2, CONFIG3, rel, rel_dev
 from oracle import schemes, tensor
 from paper_2510_21394_gb300 import inputs
 
@@ -30,7 +30,7 @@ def fc():
 
 def _rel_dev(a, b):
     torch.cuda.synchronize()
-    return float(torch.linalg.vector_norm(a.to(torch.complex128) - b) / torch.linalg.vector_norm(b))
+    return rel_dev(a, b)
 
 
 @pytest.mark.parametrize("scheme", ["lie", "etd2rk"])
@@ -47,6 +47,10 @@ def test_config2_1023x1024_500_steps(fc, scheme):
     got = s64.integrate(scheme, 1e-3, 3, v64)
     torch.cuda.synchronize()
     assert rel(got.cpu().numpy(), ref) <= TOL64
+    # the split-BF16 path on the same window, against the oracle directly
+    got32 = s32.integrate(scheme, 1e-3, 3, v64.to(torch.complex64))
+    torch.cuda.synchronize()
+    assert rel(got32.cpu().numpy().astype(np.complex128), ref) <= TOL_TC
     # (2) split-BF16 vs FP64 GPU at T = 0.5
     a = s64.integrate(scheme, 1e-3, 500, v64)
     b = s32.integrate(scheme, 1e-3, 500, v64.to(torch.complex64))
@@ -69,7 +73,11 @@ def test_config3_256cube_krogstad_200_steps(fc):
     got = s64.integrate("krogstad", 1e-3, 1, v64)
     torch.cuda.synchronize()
     assert rel(got.cpu().numpy(), ref) <= TOL64
-    del ref, got
+    # the split-BF16 path on the same step, against the oracle directly
+    got32 = s32.integrate("krogstad", 1e-3, 1, v64.to(torch.complex64))
+    torch.cuda.synchronize()
+    assert rel(got32.cpu().numpy().astype(np.complex128), ref) <= TOL_TC
+    del ref, got, got32
     # (2) split-BF16 vs FP64 GPU at T = 0.2
     a = s64.integrate("krogstad", 1e-3, 200, v64)
     b = s32.integrate("krogstad", 1e-3, 200, v64.to(torch.complex64))
