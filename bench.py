@@ -495,6 +495,7 @@ def run_ours(args, rank, world, local_rank):
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
 
     if rank == 0:
+        extra["autotune"] = fcgle.fcgle_autotune_report().strip().splitlines()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n, "bf16x3", args.scheme, args.tau),
@@ -671,6 +672,7 @@ def run_config2(args, rank, world, local_rank):
         except Exception as e:
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     if rank == 0:
+        extra["autotune"] = fcgle.fcgle_autotune_report().strip().splitlines()
         line = {"metric": METRIC, "value": per["etd2rk"]["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": per["etd2rk"]["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",

@@ -283,8 +283,30 @@ fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P);
  * X and Y hold 2 P reals each (double / float).  flags bit 1 (BF16X3 handles
  * only): X and Y are in the split form the tensor-core kernel reads and
  * writes, 4 P bf16 = the hi planes (re, im) followed by the lo planes, each
- * value being hi + lo.  X and Y must not overlap.  direction in 0..d-1. */
+ * value being hi + lo.  flags bit 2 (BF16X3 handles only, not with bit 1):
+ * the precise product used for the first and last Tucker operators of a time
+ * integration, FP32 in and out: split-TF32 (x = hi + lo, both TF32, three
+ * tensor-core products hi.hi + hi.lo + lo.hi, about 2^-21 relative) when
+ * d >= 2 and R is a multiple of 8, FP32 on the CUDA cores otherwise.  Other
+ * flag bits give FCGLE_ERR_INVALID_ARG.  X and Y must not overlap.  direction
+ * in 0..d-1. */
 fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y);
+
+/* The kernel autotuner (a library facility, not a step of the method).  The
+ * split-BF16 plain mode product has several shared-memory ring
+ * configurations (X ring 4 / 3 / 2 deep with the M ring taking the rest, or
+ * the block of M resident in shared memory for p <= 256); the best one
+ * depends on the contracted extent p and on the number of units per SM.
+ * fcgle_setup and fcgle_batch_create time every eligible configuration once
+ * per process for each new (p, R) a handle runs the plain product on, on the
+ * handle's work buffers (synchronously, a few kernel launches each), and the
+ * fastest is used from then on.  The environment variable FCGLE_PLAIN_CFG=<id>
+ * (0..3, read once) forces one configuration where it is eligible.
+ * This call writes a text report, one line per tuned shape with the time of
+ * every eligible configuration and the choice, into buf (size bytes,
+ * NUL-terminated, truncated if short) and the full length + 1 into *needed
+ * (either pointer may be NULL). */
+fcgle_status fcgle_autotune_report(char* buf, size_t size, size_t* needed);
 
 /* Number of kernel launches this handle has issued since setup (all
  * entry points; used to report launch counts). */

@@ -28,12 +28,40 @@
 // tensor maps and sizes of problem k come from the descriptor gd[k], which
 // owns the global units [gd[k].ubegin, gd[k + 1].ubegin).  The arithmetic per
 // unit is the same as in the single form.
+//
+// Operand formats (OP):
+//   kOpBF16   split-BF16 in and out: x = hi + lo, two bf16 each; products
+//             hi.hi + hi.lo + lo.hi with tcgen05.mma kind::f16 (K = 16).
+//   kOpTF32   split-TF32 in and out: x = hi + lo, two FP32 words each holding
+//             a TF32 value (hi = x rounded to TF32, lo = x - hi rounded to
+//             TF32, about 21 significant bits together); the same three
+//             products with kind::tf32 (K = 8).  A 128-byte shared-memory row
+//             holds 32 TF32 values instead of 64 bf16, so a k-chunk is 32 wide
+//             and every stage, box and descriptor keeps its byte layout.
+//   kOpTF32F  split-TF32 in, plain FP32 out (the last product of a Tucker
+//             operator whose result is an FP32 tensor).
+// The TF32 forms serve the precise transforms at the two ends of a time
+// integration, where the split-BF16 error (about 2^-17 per product) must not
+// enter the state.
+//
+// Resident-M form (MR = true, single form only): when the grid is a multiple
+// of m_blocks every CTA works on one fixed i-block (u = blockIdx.x + j gridDim.x
+// keeps u % m_blocks), so with k_chunks <= 4 (p <= 256 for bf16) the CTA loads
+// its 128 x p block of M once, into a 128 KB resident region, instead of
+// streaming it from L2 for every unit; the X ring is then 2 deep.  This halves
+// the operand bytes each SM pulls through L2 per unit at p = 256.
 #pragma once
 
 #include "b3_kernel.cuh"
 
 namespace fcgle {
 namespace b3 {
+
+constexpr int kOpBF16 = 0, kOpTF32 = 1, kOpTF32F = 2;
+
+// elements of one 128-byte operand row (the k extent of a chunk)
+template <int OP>
+constexpr int chunk_k() { return OP == kOpBF16 ? 64 : 32; }
 
 constexpr int PL_NX = 4;                   // X ring depth
 constexpr int PL_NM = 2;                   // M ring depth
@@ -55,12 +83,43 @@ struct PlainDesc {
   long long ubegin;
 };
 
-template <bool G>
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// x rounded to TF32 (10 explicit mantissa bits, ties away from zero), as an FP32 word
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+constexpr int kMRMaxChunks = 4;   // resident M: up to 4 chunks of 32 KB
+constexpr int kMaxRing = 4;       // barrier slots per ring
+
+// Ring configurations of the single form (X ring depth NXR; the M ring takes
+// the rest of the 192 KB operand area, or the resident region when MR):
+//   NXR = 4: X 4 x 32 KB + M 2 x 32 KB (the default, and the grouped form)
+//   NXR = 3: X 3 + M 3;  NXR = 2: X 2 + M 4 (long k extents: more M in flight)
+//   MR:      X 2 + resident M (p <= 256)
+template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false>
 __global__ void __launch_bounds__(PL_THREADS, 1)
     mp_b3_plain_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                        const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                        const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                        const KParams kp, const PlainDesc* __restrict__ gd, int ngd, long long gunits) {
+  static_assert(!(G && (MR || NXR != PL_NX)), "the grouped form uses the default rings");
+  // X ring depth and the offset of the M region (ring or resident); the
+  // epilogue staging area starts at the same offset in every configuration
+  constexpr int NX = MR ? 2 : NXR;
+  constexpr int NM = MR ? kMRMaxChunks : (int)((kPlOffEpi - NX * kXStage) / kMStage);
+  constexpr uint32_t kOffM = NX * kXStage;
+  static_assert(NX >= 2 && NX <= kMaxRing && NM >= 2 && NM <= kMaxRing, "ring depths");
+  static_assert(kOffM + NM * kMStage == kPlOffEpi, "shared memory layout");
   extern __shared__ uint8_t smem_raw[];
   pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -69,22 +128,20 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kPlOffBar);
   auto full_x = [&](int s) { return smem_u32(&bars[s]); };
-  auto empty_x = [&](int s) { return smem_u32(&bars[PL_NX + s]); };
-  auto full_m = [&](int s) { return smem_u32(&bars[2 * PL_NX + s]); };
-  auto empty_m = [&](int s) { return smem_u32(&bars[2 * PL_NX + PL_NM + s]); };
-  auto acc_full = [&](int a) { return smem_u32(&bars[2 * PL_NX + 2 * PL_NM + a]); };
-  auto acc_empty = [&](int a) { return smem_u32(&bars[2 * PL_NX + 2 * PL_NM + 2 + a]); };
-  const uint32_t fin_bar = smem_u32(&bars[2 * PL_NX + 2 * PL_NM + 4]);
-  static_assert((2 * PL_NX + 2 * PL_NM + 5) * 8 <= 192, "barrier area");
+  auto empty_x = [&](int s) { return smem_u32(&bars[kMaxRing + s]); };
+  auto full_m = [&](int s) { return smem_u32(&bars[2 * kMaxRing + s]); };
+  auto empty_m = [&](int s) { return smem_u32(&bars[3 * kMaxRing + s]); };
+  auto acc_full = [&](int a) { return smem_u32(&bars[4 * kMaxRing + a]); };
+  auto acc_empty = [&](int a) { return smem_u32(&bars[4 * kMaxRing + 2 + a]); };
+  const uint32_t fin_bar = smem_u32(&bars[4 * kMaxRing + 4]);
+  static_assert((4 * kMaxRing + 5) * 8 <= 192, "barrier area");
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kPlOffBar + 192);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kPlOffBar + 200);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PL_NX; ++s) {
+    for (int s = 0; s < kMaxRing; ++s) {
       mbar_init(full_x(s), 1);
       mbar_init(empty_x(s), 1);
-    }
-    for (int s = 0; s < PL_NM; ++s) {
       mbar_init(full_m(s), 1);
       mbar_init(empty_m(s), 1);
     }
@@ -139,23 +196,37 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         const int r0 = (int)(tile * BR);
         const int r1 = (int)(R + tile * BR);   // same r in the imaginary plane
         for (int kc = 0; kc < KC; ++kc, ++g) {
-          const int s = (int)(g % PL_NX);
-          if (!mbar_wait(empty_x(s), ((g / PL_NX) & 1) ^ 1, abort_flag, err, 11)) { ok = false; break; }
+          const int s = (int)(g % NX);
+          if (!mbar_wait(empty_x(s), ((g / NX) & 1) ^ 1, abort_flag, err, 11)) { ok = false; break; }
           const uint32_t st = sbase + s * kXStage;
           mbar_arrive_tx(full_x(s), kXStage);
-          tma_load_2d(st, mxh, kc * BK, r0, full_x(s));
-          tma_load_2d(st + 8192, mxh, kc * BK, r1, full_x(s));
-          tma_load_2d(st + 16384, mxl, kc * BK, r0, full_x(s));
-          tma_load_2d(st + 24576, mxl, kc * BK, r1, full_x(s));
+          constexpr int CK = chunk_k<OP>();
+          tma_load_2d(st, mxh, kc * CK, r0, full_x(s));
+          tma_load_2d(st + 8192, mxh, kc * CK, r1, full_x(s));
+          tma_load_2d(st + 16384, mxl, kc * CK, r0, full_x(s));
+          tma_load_2d(st + 24576, mxl, kc * CK, r1, full_x(s));
         }
       }
       const uint32_t issued = g;
-      for (uint32_t q = issued >= PL_NX ? issued - PL_NX : 0; q < issued; ++q)
-        mbar_wait(full_x(q % PL_NX), (q / PL_NX) & 1, abort_flag, err, 17, true);
+      for (uint32_t q = issued >= (uint32_t)NX ? issued - NX : 0; q < issued; ++q)
+        mbar_wait(full_x(q % NX), (q / NX) & 1, abort_flag, err, 17, true);
     }
   } else if (warp == 2) {
     // ------------------------------------------------------------ M producer
-    if (lane == 0) {
+    if (MR && lane == 0) {
+      // the CTA's fixed i-block of M, all k-chunks, loaded once
+      if ((long long)blockIdx.x < units) {
+        const int mb = (int)(blockIdx.x % kp.m_blocks);
+        constexpr int CK = chunk_k<OP>();
+        mbar_arrive_tx(full_m(0), (uint32_t)kp.k_chunks * kMStage);
+        for (int kc = 0; kc < kp.k_chunks; ++kc) {
+          const uint32_t st = sbase + kOffM + kc * kMStage;
+          tma_load_2d(st, &tm_mhi, kc * CK, mb * BM, full_m(0));
+          tma_load_2d(st + 16384, &tm_mlo, kc * CK, mb * BM, full_m(0));
+        }
+        mbar_wait(full_m(0), 0, abort_flag, err, 18, true);
+      }
+    } else if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
       int pid = 0;
@@ -172,26 +243,30 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         }
         const int mb = (int)(lu % mbk);
         for (int kc = 0; kc < KC; ++kc, ++g) {
-          const int s = (int)(g % PL_NM);
-          if (!mbar_wait(empty_m(s), ((g / PL_NM) & 1) ^ 1, abort_flag, err, 12)) { ok = false; break; }
-          const uint32_t st = sbase + kPlOffM + s * kMStage;
+          const int s = (int)(g % NM);
+          if (!mbar_wait(empty_m(s), ((g / NM) & 1) ^ 1, abort_flag, err, 12)) { ok = false; break; }
+          const uint32_t st = sbase + kOffM + s * kMStage;
           mbar_arrive_tx(full_m(s), kMStage);
-          tma_load_2d(st, mmh, kc * BK, mb * BM, full_m(s));
-          tma_load_2d(st + 16384, mml, kc * BK, mb * BM, full_m(s));
+          constexpr int CK = chunk_k<OP>();
+          tma_load_2d(st, mmh, kc * CK, mb * BM, full_m(s));
+          tma_load_2d(st + 16384, mml, kc * CK, mb * BM, full_m(s));
         }
       }
       const uint32_t issued = g;
-      for (uint32_t q = issued >= PL_NM ? issued - PL_NM : 0; q < issued; ++q)
-        mbar_wait(full_m(q % PL_NM), (q / PL_NM) & 1, abort_flag, err, 18, true);
+      for (uint32_t q = issued >= (uint32_t)NM ? issued - NM : 0; q < issued; ++q)
+        mbar_wait(full_m(q % NM), (q / NM) & 1, abort_flag, err, 18, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+      // instruction descriptor: FP32 accumulator; A, B bf16 (1) or tf32 (2); K-major; N, M
+      constexpr uint32_t kAB = OP == kOpBF16 ? 1u : 2u;
+      constexpr uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(BN >> 3) << 17) |
                                  ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
       bool ok = true;
       int pid = 0;
+      if (MR && (long long)blockIdx.x < units) ok = mbar_wait(full_m(0), 0, abort_flag, err, 14);
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
         int KC = kp.k_chunks;
         if constexpr (G) {
@@ -203,22 +278,29 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + a * BN;
         for (int kc = 0; kc < KC; ++kc, ++g) {
-          const int sx = (int)(g % PL_NX), sm = (int)(g % PL_NM);
-          if (!mbar_wait(full_m(sm), (g / PL_NM) & 1, abort_flag, err, 14)) { ok = false; break; }
-          if (!mbar_wait(full_x(sx), (g / PL_NX) & 1, abort_flag, err, 15)) { ok = false; break; }
+          const int sx = (int)(g % NX), sm = MR ? kc : (int)(g % NM);
+          if (!MR && !mbar_wait(full_m(sm), (g / NM) & 1, abort_flag, err, 14)) { ok = false; break; }
+          if (!mbar_wait(full_x(sx), (g / NX) & 1, abort_flag, err, 15)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ahi = sbase + kPlOffM + sm * kMStage, alo = ahi + 16384;
+          const uint32_t ahi = sbase + kOffM + sm * kMStage, alo = ahi + 16384;
           const uint32_t bhi = sbase + sx * kXStage, blo = bhi + 16384;
+          // four k-steps of 32 bytes per 128-byte row (K = 16 bf16 or 8 tf32 each)
 #pragma unroll
-          for (int ks = 0; ks < BK / 16; ++ks) {
+          for (int ks = 0; ks < 4; ++ks) {
             const uint32_t off = ks * 32;
             const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-            mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
-            mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
-            mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+            if constexpr (OP == kOpBF16) {
+              mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
+              mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
+              mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+            } else {
+              mma_tf32(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
+              mma_tf32(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
+              mma_tf32(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+            }
           }
           mma_commit(empty_x(sx));
-          mma_commit(empty_m(sm));
+          if (!MR) mma_commit(empty_m(sm));
         }
         if (!ok) break;
         mma_commit(acc_full(a));
@@ -261,6 +343,49 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(a));
       const int i_base = mb * BM + q * 32;
+      if constexpr (OP != kOpBF16) {
+        // FP32 boxes of 32 x 32 (128-byte rows), one at a time through the 4 KB
+        // staging area: per component the hi words (kOpTF32F: the FP32 value),
+        // then (kOpTF32) the lo words
+        float* fbox = reinterpret_cast<float*>(box);
+        constexpr int NPART = OP == kOpTF32 ? 2 : 1;
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+#pragma unroll
+          for (int part = 0; part < NPART; ++part) {
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+#pragma unroll
+            for (int g2 = 0; g2 < 2; ++g2) {
+              const uint32_t* v = comp == 0 ? vr[g2] : vi[g2];
+#pragma unroll
+              for (int j = 0; j < 16; j += 4) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float x = __uint_as_float(v[j + e]);
+                  if constexpr (OP == kOpTF32F) {
+                    o[e] = x;
+                  } else {
+                    const float h = tf32_round(x);
+                    o[e] = part == 0 ? h : tf32_round(x - h);
+                  }
+                }
+                *reinterpret_cast<float4*>(fbox + lane * 32 + g2 * 16 + j) = make_float4(o[0], o[1], o[2], o[3]);
+              }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              const int x = (int)(tile * BR + 32 * half);
+              tma_store_3d(part == 0 ? myh : myl, smem_u32(fbox), x, i_base, comp);
+              bulk_commit();
+            }
+            __syncwarp();
+          }
+        }
+        continue;
+      }
       // this warp's two groups are adjacent (cc = 2 half, 2 half + 1): one 32 x 32 box
       // (64-byte rows) per component, real part first, then imaginary part
 #pragma unroll

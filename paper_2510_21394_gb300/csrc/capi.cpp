@@ -148,6 +148,7 @@ fcgle_status fcgle_setup(const fcgle_params* params, void* cuda_stream, fcgle_ha
       ctx->prm = *params;
       ctx->stream = (cudaStream_t)cuda_stream;
       ctx->eng = make_engine(*params, ctx->stream);
+      ctx->eng->autotune();
     } catch (...) {
       delete ctx;
       throw;
@@ -344,7 +345,8 @@ fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const 
     check_handle(h);
     if (!X || !Y) throw InvalidArg("tensor pointer is NULL");
     if (X == Y) throw InvalidArg("X and Y must not overlap");
-    h->eng->mode_product_flags(direction, flags & 3, X, Y);
+    if (flags & ~7) throw InvalidArg("unknown flags");
+    h->eng->mode_product_flags(direction, flags, X, Y);
   });
 }
 
@@ -459,6 +461,9 @@ fcgle_status fcgle_batch_create(int count, const fcgle_params* params, void* cud
       for (auto& t : th) t.join();
       for (int i = 0; i < count; ++i)
         if (!b->inst[i]) throw std::runtime_error("instance " + std::to_string(i) + ": " + errs[i]);
+      // timing runs one instance at a time, so that no other work overlaps them
+      FCGLE_CUDA(cudaDeviceSynchronize());
+      for (auto* h : b->inst) h->eng->autotune();
     } catch (...) {
       batch_free(b);
       throw;
@@ -690,6 +695,18 @@ fcgle_status fcgle_batch_launch_count(fcgle_batch b, long long* kernels, long lo
 
 fcgle_status fcgle_batch_destroy(fcgle_batch b) {
   return guarded([&] { batch_free(b); });
+}
+
+fcgle_status fcgle_autotune_report(char* buf, size_t size, size_t* needed) {
+  return guarded([&] {
+    const std::string r = plain_tune_report();
+    if (needed) *needed = r.size() + 1;
+    if (buf && size > 0) {
+      const size_t n = std::min(size - 1, r.size());
+      std::memcpy(buf, r.data(), n);
+      buf[n] = 0;
+    }
+  });
 }
 
 const char* fcgle_status_string(fcgle_status s) {

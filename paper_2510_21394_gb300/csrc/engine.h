@@ -50,9 +50,10 @@ class EngineBase {
   virtual void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target,
                        int ckpt_every, void* grad_u0, double* grad_params, double* loss) = 0;
   virtual void mode_product(int mu, bool fwd, const void* X, void* Y) = 0;
-  // flags: bit 0 forward (Q^T), bit 1 split-bf16 input and output (BF16X3 only)
+  // flags: bit 0 forward (Q^T), bit 1 split-bf16 input and output, bit 2 the
+  // precise (split-TF32) product on FP32 input and output (bits 1, 2: BF16X3 only)
   virtual void mode_product_flags(int mu, int flags, const void* X, void* Y) {
-    if (flags & 2) throw InvalidArg("split input/output needs a BF16X3 handle");
+    if (flags & 6) throw InvalidArg("flags bits 1 and 2 need a BF16X3 handle");
     mode_product(mu, flags & 1, X, Y);
   }
   virtual size_t internal_elems() const = 0;
@@ -71,6 +72,9 @@ class EngineBase {
   virtual bool time_dependent() const = 0;
   virtual size_t elem_bytes() const = 0;
   virtual int device_error() = 0;   // reads and clears the device error flag (synchronises)
+  // times the kernel configurations this handle can choose between and records
+  // the fastest (process-wide, per problem shape); synchronous; no-op by default
+  virtual void autotune() {}
   // Grouped batch launches: while a recorder is set, every mode product of
   // one_step is recorded (as a kernel descriptor) instead of launched.
   // Returns false if the engine has no grouped form (FP64, d == 1).
@@ -94,6 +98,8 @@ struct GroupRec {
 Direction spectral_direction(const fcgle_params& prm, int mu);
 
 std::unique_ptr<EngineBase> make_engine(const fcgle_params& prm, cudaStream_t st);
+// the plain-product autotuner's timings and choices so far, one line per shape
+std::string plain_tune_report();
 std::unique_ptr<EngineBase> make_engine_b3(const fcgle_params& prm, cudaStream_t st);
 
 }  // namespace fcgle

@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <cstdio>
 #include <complex>
 #include <cstdlib>
 #include <cstring>
@@ -79,6 +80,76 @@ void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaSt
   FCGLE_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...));
 }
 
+// ------------------------------------------------ plain-product autotuner
+// Ring configurations of the plain mode product (b3_plain.cuh); which one is
+// fastest depends on the contracted extent p (k-chunks per unit) and on how
+// many units each SM gets, so each distinct (p, R) is timed once per process
+// (all eligible configurations, on the handle's own work buffers, at setup) and
+// the fastest is used from then on.  FCGLE_PLAIN_CFG=<id> (read once) forces
+// one configuration where it is eligible.
+enum PlainCfg { kCfgX4M2 = 0, kCfgX3M3 = 1, kCfgX2M4 = 2, kCfgMR = 3, kNumPlainCfg = 4 };
+const char* const kPlainCfgName[kNumPlainCfg] = {"X4M2", "X3M3", "X2M4", "residentM"};
+
+using PlainKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
+                             b3::KParams, const b3::PlainDesc*, int, long long);
+
+PlainKernel plain_kernel(int cfg) {
+  switch (cfg) {
+    case kCfgX3M3: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 3>;
+    case kCfgX2M4: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2>;
+    case kCfgMR: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, true>;
+    default: return b3::mp_b3_plain_kernel<false>;
+  }
+}
+
+int forced_plain_cfg() {
+  static const int c = [] {
+    const char* e = std::getenv("FCGLE_PLAIN_CFG");
+    if (!e || !*e) return -1;
+    const int v = std::atoi(e);
+    return (v >= 0 && v < kNumPlainCfg) ? v : -1;
+  }();
+  return c;
+}
+
+struct TuneEntry {
+  int cfg = kCfgX4M2;
+  float us[kNumPlainCfg] = {-1.f, -1.f, -1.f, -1.f};   // -1: not eligible
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, long long>, TuneEntry> g_tune;   // (p, R)
+
+bool tuned_lookup(int p, long long R, TuneEntry& e) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(p, R));
+  if (it == g_tune.end()) return false;
+  e = it->second;
+  return true;
+}
+
+}  // namespace
+
+// Text report of the autotuner's choices (C ABI: fcgle_autotune_report).
+std::string plain_tune_report() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string out;
+  char line[256];
+  for (const auto& kv : g_tune) {
+    int n = std::snprintf(line, sizeof(line), "plain p=%d R=%lld:", std::get<0>(kv.first), std::get<1>(kv.first));
+    out.append(line, (size_t)n);
+    for (int c = 0; c < kNumPlainCfg; ++c)
+      if (kv.second.us[c] >= 0.f) {
+        n = std::snprintf(line, sizeof(line), " %s %.2fus", kPlainCfgName[c], kv.second.us[c]);
+        out.append(line, (size_t)n);
+      }
+    n = std::snprintf(line, sizeof(line), " -> %s\n", kPlainCfgName[kv.second.cfg]);
+    out.append(line, (size_t)n);
+  }
+  return out;
+}
+
+namespace {
+
 int num_sms() {
   static const int sms = [] {   // thread-safe one-time initialisation
     int dev = 0, m = 0;
@@ -124,6 +195,43 @@ void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p)
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
+}
+
+// 2D FP32 tensor map, SWIZZLE_128B, box (32 inner = 128 bytes, box_rows outer):
+// split-TF32 operands of the precise transforms.
+void encode_f32(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
+}
+
+// 3D FP32 tensor map over an output plane pair [2][p][R], box (32, 32, 1), no swizzle.
+void encode_f32_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p) {
+  cuuint64_t dims[3] = {R, p, 2};
+  cuuint64_t strides[2] = {R * 4, R * p * 4};
+  cuuint32_t box[3] = {32, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw std::runtime_error("cuTensorMapEncodeTiled (f32 store) failed (" + std::to_string((int)r) + ")");
+}
+
+// x rounded to TF32 on the host (10 explicit mantissa bits, ties away from
+// zero), the same rounding as the device's cvt.rna.tf32.f32 for finite x
+float tf32_rna_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & ~0x1FFFu;
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
 }
 
 // ------------------------------------------------------ standalone kernels
@@ -177,6 +285,22 @@ __global__ void flow_incr_split_kernel(uint32_t P, b3::Flow f, const float* __re
 #pragma unroll
     for (int v = 0; v < 4; ++v) b3::flow_incr(f, ur[v], ui[v], vr[v], vi[v]);
     b3::put_csplit<4>(V, P, q, vr, vi);
+  }
+}
+
+// FP32 -> split-TF32: hi = tf32(x), lo = tf32(x - hi); n % 4 == 0
+__global__ void tf32_split_kernel(uint32_t n, const float* __restrict__ X, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < n; q += 4 * gridDim.x * blockDim.x) {
+    float x[4], h[4], l[4];
+    b3::ldv<4>(X + q, x);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      h[v] = b3::tf32_round(x[v]);
+      l[v] = b3::tf32_round(x[v] - h[v]);
+    }
+    b3::stv<4>(hi + q, h);
+    b3::stv<4>(lo + q, l);
   }
 }
 
@@ -301,6 +425,13 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiStrangB>();
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
+      for (int c = 0; c < kNumPlainCfg; ++c)
+        FCGLE_CUDA(cudaFuncSetAttribute(plain_kernel(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)b3::kPlSmemBytes));
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false, b3::kOpTF32>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b3::kPlSmemBytes));
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false, b3::kOpTF32F>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b3::kPlSmemBytes));
     });
   }
 
@@ -310,6 +441,8 @@ class EngineB3 : public EngineBase {
         if (mat_[mu][f].hi) cudaFree(mat_[mu][f].hi);
         if (mat_[mu][f].lo) cudaFree(mat_[mu][f].lo);
         if (mat_[mu][f].f32) cudaFree(mat_[mu][f].f32);
+        if (mat_[mu][f].thi) cudaFree(mat_[mu][f].thi);
+        if (mat_[mu][f].tlo) cudaFree(mat_[mu][f].tlo);
       }
   }
 
@@ -370,6 +503,22 @@ class EngineB3 : public EngineBase {
   void mode_product_flags(int mu, int flags, const void* X, void* Y) override {
     if (mu < 0 || mu >= s_.d) throw InvalidArg("direction must be in 0..d-1");
     const bool fwd = flags & 1;
+    if (flags & 4) {
+      // the precise form of the end transforms: FP32 planar in and out
+      if (flags & 2) throw InvalidArg("flags bits 1 and 2 exclude each other");
+      const long long R = P_ / s_.p[mu];
+      if (s_.d >= 2 && R % 8 == 0) {
+        for (int k = 0; k < 2; ++k)
+          if (!tsp_[k]) tsp_[k].reset(new DevMem<float>(4 * s_.P));
+        float* A = tsp_[0]->ptr;
+        tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), (const float*)X, A, A + 2 * s_.P);
+        FCGLE_LAUNCHED(launches);
+        launch_tf32(A, A + 2 * s_.P, mu, fwd, (float*)Y, nullptr);
+      } else {
+        mp_f32((const float*)X, (float*)Y, mat_[mu][fwd ? 0 : 1].f32, s_.p[mu], (size_t)R, st_, launches);
+      }
+      return;
+    }
     if (flags & 2) {
       const __nv_bfloat16* xh = (const __nv_bfloat16*)X;
       __nv_bfloat16* yh = (__nv_bfloat16*)Y;
@@ -494,9 +643,12 @@ class EngineB3 : public EngineBase {
   struct Mat {
     __nv_bfloat16* hi = nullptr;
     __nv_bfloat16* lo = nullptr;
-    float* f32 = nullptr;   // p x p, for the FP32 transforms at the ends of a time integration
-    int p = 0, m_pad = 0, k_pad = 0;
-    CUtensorMap tm_hi, tm_lo;
+    float* f32 = nullptr;   // p x p FP32 (the CUDA-core form of the precise transforms, d == 1)
+    // split-TF32 hi / lo (m_pad x k_pad32): the tensor-core form of the precise transforms
+    float* thi = nullptr;
+    float* tlo = nullptr;
+    int p = 0, m_pad = 0, k_pad = 0, k_pad32 = 0;
+    CUtensorMap tm_hi, tm_lo, tm_thi, tm_tlo;
   };
 
   float* F32(int i) { return f32_[i]->ptr; }
@@ -532,12 +684,84 @@ class EngineB3 : public EngineBase {
     for (size_t e = 0; e < f.size(); ++e) f[e] = (float)M[e];
     FCGLE_CUDA(cudaMalloc(&m.f32, f.size() * 4));
     FCGLE_CUDA(cudaMemcpy(m.f32, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    // split-TF32: hi = tf32(M), lo = tf32(M - hi), zero padded to (m_pad, k_pad32)
+    m.k_pad32 = (p + 31) / 32 * 32;
+    std::vector<float> th((size_t)m.m_pad * m.k_pad32, 0.0f), tl(th);
+    for (int i = 0; i < p; ++i)
+      for (int k = 0; k < p; ++k) {
+        const double x = M[(size_t)i * p + k];
+        const float h = tf32_rna_host((float)x);
+        th[(size_t)i * m.k_pad32 + k] = h;
+        tl[(size_t)i * m.k_pad32 + k] = tf32_rna_host((float)(x - (double)h));
+      }
+    FCGLE_CUDA(cudaMalloc(&m.thi, th.size() * 4));
+    FCGLE_CUDA(cudaMalloc(&m.tlo, tl.size() * 4));
+    FCGLE_CUDA(cudaMemcpy(m.thi, th.data(), th.size() * 4, cudaMemcpyHostToDevice));
+    FCGLE_CUDA(cudaMemcpy(m.tlo, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice));
+    encode_f32(&m.tm_thi, m.thi, m.k_pad32, m.m_pad, b3::BM);
+    encode_f32(&m.tm_tlo, m.tlo, m.k_pad32, m.m_pad, b3::BM);
   }
 
-  // Tucker operator in FP32 on the CUDA cores (X, Y planar FP32, distinct);
-  // used where the split-BF16 error must not enter: U^_0 = fwd(u_0) at the
-  // start of a time integration and u(T) = bwd(U^_T) at its end.
+  // Precise Tucker operator (X, Y planar FP32, distinct), used where the
+  // split-BF16 error must not enter: U^_0 = fwd(u_0) at the start of a time
+  // integration and u(T) = bwd(U^_T) at its end.  Split-TF32 on the tensor
+  // cores (about 2^-21 relative per product) when every output row pitch
+  // allows the FP32 TMA boxes (d >= 2, R % 8 == 0); FP32 on the CUDA cores
+  // otherwise.
   void tucker_f32(const float* X, float* Y, bool fwd) {
+    bool tc = s_.d >= 2;
+    for (int mu = 0; mu < s_.d && tc; ++mu) tc = (P_ / s_.p[mu]) % 8 == 0;
+    if (tc) {
+      tucker_tf32(X, Y, fwd);
+      return;
+    }
+    tucker_simt(X, Y, fwd);
+  }
+
+  void tucker_tf32(const float* X, float* Y, bool fwd) {
+    for (int k = 0; k < 2; ++k)
+      if (!tsp_[k]) tsp_[k].reset(new DevMem<float>(4 * s_.P));   // hi planes (2 P), then lo planes (2 P)
+    float* A = tsp_[0]->ptr;
+    float* B = tsp_[1]->ptr;
+    tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), X, A, A + 2 * s_.P);
+    FCGLE_LAUNCHED(launches);
+    const float* src = A;
+    for (int mu = 0; mu < s_.d; ++mu) {
+      const bool last = mu == s_.d - 1;
+      float* dst = last ? Y : (src == A ? B : A);
+      launch_tf32(src, src + 2 * s_.P, mu, fwd, dst, last ? nullptr : dst + 2 * s_.P);
+      src = dst;
+    }
+  }
+
+  // one split-TF32 mode product; ylo == nullptr: plain FP32 output into yhi
+  void launch_tf32(const float* xh, const float* xl, int mu, bool fwd, float* yhi, float* ylo) {
+    const Mat& m = mat_[mu][fwd ? 0 : 1];
+    const long long R = P_ / s_.p[mu];
+    CUtensorMap txh, txl, tyh, tyl;
+    encode_f32(&txh, xh, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    encode_f32(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+    encode_f32_out(&tyh, yhi, (uint64_t)R, (uint64_t)s_.p[mu]);
+    encode_f32_out(&tyl, ylo ? ylo : yhi, (uint64_t)R, (uint64_t)s_.p[mu]);
+    b3::KParams kp;
+    kp.R = R;
+    kp.p = s_.p[mu];
+    kp.m_blocks = m.m_pad / b3::BM;
+    kp.k_chunks = m.k_pad32 / 32;
+    kp.tiles = (R + b3::BR - 1) / b3::BR;
+    kp.err = err_->ptr;
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    if (ylo)
+      launch_pdl(b3::mp_b3_plain_kernel<false, b3::kOpTF32>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl,
+                 m.tm_thi, m.tm_tlo, tyh, tyl, kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
+    else
+      launch_pdl(b3::mp_b3_plain_kernel<false, b3::kOpTF32F>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl,
+                 m.tm_thi, m.tm_tlo, tyh, tyl, kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  void tucker_simt(const float* X, float* Y, bool fwd) {
     float* tmp[2] = {F32(kFh), F32(kD2)};
     const float* src = X;
     for (int mu = 0; mu < s_.d; ++mu) {
@@ -589,10 +813,98 @@ class EngineB3 : public EngineBase {
       record(false, &launch_plain_grouped, offsetof(b3::PlainDesc, ubegin), &d, sizeof(d), units);
       return;
     }
-    launch_pdl(b3::mp_b3_plain_kernel<false>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl, m.tm_hi,
-               m.tm_lo, tyh, tyl, kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
+    int cfg = forced_plain_cfg();
+    if (cfg < 0 || !plain_cfg_ok(cfg, kp, units)) {
+      TuneEntry e;
+      cfg = tuned_lookup(kp.p, R, e) ? e.cfg : default_plain_cfg(kp, units);
+    }
+    launch_plain_cfg(cfg, txh, txl, m, tyh, tyl, kp, units);
+  }
+
+  // resident M: every CTA keeps one fixed i-block (grid a multiple of m_blocks)
+  // and the block of M fits the 4 x 32 KB resident region
+  static int grid_mr(long long units, int m_blocks) {
+    const int sms = num_sms();
+    return units < sms ? (int)units : sms - sms % m_blocks;
+  }
+  static bool plain_cfg_ok(int cfg, const b3::KParams& kp, long long units) {
+    if (cfg != kCfgMR) return true;
+    return kp.k_chunks <= b3::kMRMaxChunks && grid_mr(units, kp.m_blocks) >= kp.m_blocks;
+  }
+  static int default_plain_cfg(const b3::KParams& kp, long long units) {
+    return plain_cfg_ok(kCfgMR, kp, units) ? kCfgMR : kCfgX4M2;
+  }
+  void launch_plain_cfg(int cfg, const CUtensorMap& txh, const CUtensorMap& txl, const Mat& m, const CUtensorMap& tyh,
+                        const CUtensorMap& tyl, const b3::KParams& kp, long long units) {
+    const int grid = cfg == kCfgMR ? grid_mr(units, kp.m_blocks) : (int)std::min<long long>(units, num_sms());
+    launch_pdl(plain_kernel(cfg), grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl, m.tm_hi, m.tm_lo, tyh, tyl,
+               kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
     FCGLE_LAUNCHED(launches);
   }
+
+ public:
+  // Times every eligible ring configuration of the plain product for each
+  // direction this handle runs it on (directions 0 .. d-2; the last direction
+  // carries the fused epilogues) whose (p, R) the process has not tuned yet,
+  // on the handle's work buffers, and records the fastest.  Synchronous.
+  void autotune() override {
+    if (forced_plain_cfg() >= 0) return;
+    for (int mu = 0; mu + 1 < s_.d; ++mu) {
+      const long long R = P_ / s_.p[mu];
+      if (R % 8 != 0) continue;
+      TuneEntry have;
+      if (tuned_lookup(s_.p[mu], R, have)) continue;
+      const Mat& m = mat_[mu][0];
+      SplitOut in = SP(kT0), out = SP(kT1);
+      CUtensorMap txh, txl, tyh, tyl;
+      encode_bf16(&txh, in.hi, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+      encode_bf16(&txl, in.lo, (uint64_t)s_.p[mu], 2 * (uint64_t)R, b3::BR);
+      encode_bf16_out(&tyh, out.hi, (uint64_t)R, (uint64_t)s_.p[mu]);
+      encode_bf16_out(&tyl, out.lo, (uint64_t)R, (uint64_t)s_.p[mu]);
+      b3::KParams kp;
+      kp.R = R;
+      kp.p = s_.p[mu];
+      kp.m_blocks = m.m_pad / b3::BM;
+      kp.k_chunks = m.k_pad / b3::BK;
+      kp.tiles = (R + b3::BR - 1) / b3::BR;
+      kp.err = err_->ptr;
+      const long long units = kp.tiles * kp.m_blocks;
+      TuneEntry e;
+      float best = 0.f;
+      cudaEvent_t e0, e1;
+      FCGLE_CUDA(cudaEventCreate(&e0));
+      FCGLE_CUDA(cudaEventCreate(&e1));
+      try {
+        constexpr int kReps = 5;
+        for (int c = 0; c < kNumPlainCfg; ++c) {
+          if (!plain_cfg_ok(c, kp, units)) continue;
+          launch_plain_cfg(c, txh, txl, m, tyh, tyl, kp, units);   // warm-up
+          FCGLE_CUDA(cudaEventRecord(e0, st_));
+          for (int r = 0; r < kReps; ++r) launch_plain_cfg(c, txh, txl, m, tyh, tyl, kp, units);
+          FCGLE_CUDA(cudaEventRecord(e1, st_));
+          FCGLE_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          FCGLE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          e.us[c] = 1e3f * ms / kReps;
+          if (best == 0.f || e.us[c] < best) {
+            best = e.us[c];
+            e.cfg = c;
+          }
+        }
+      } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (device_error()) throw DeviceTimeout("a bounded device-side wait gave up while tuning the mode product");
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune.emplace(std::make_tuple(s_.p[mu], R), e);
+    }
+  }
+
+ private:
 
   // ---- grouped launches (batches): recording and the launchers
   void record(bool last, void (*fn)(const void*, int, long long, cudaStream_t), size_t uoff, const void* d,
@@ -916,6 +1228,7 @@ class EngineB3 : public EngineBase {
   std::unique_ptr<DevMem<__nv_bfloat16>> sp_[kNumSplit];
   std::unique_ptr<DevMem<float>> src_[kMaxSrc];
   std::unique_ptr<DevMem<float>> host_stage_;
+  std::unique_ptr<DevMem<float>> tsp_[2];   // split-TF32 work tensors of the precise transforms
   std::unique_ptr<DevMem<double>> scratch_;
   std::unique_ptr<DevMem<int>> err_;
 };

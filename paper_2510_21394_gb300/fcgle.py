@@ -42,7 +42,8 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_launch_count", "fcgle_destroy", "fcgle_status_string", "fcgle_last_error",
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
-           "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait", "fcgle_spectral_scalars"]
+           "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait", "fcgle_spectral_scalars",
+           "fcgle_autotune_report"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -92,6 +93,7 @@ def _load():
         "fcgle_norm_static": [ctypes.POINTER(fcgle_params), P, P, ctypes.POINTER(D)],
         "fcgle_selftest_bounded_wait": [P, ctypes.POINTER(I)],
         "fcgle_spectral_scalars": [H, I, I, D, I, ctypes.POINTER(D), ctypes.POINTER(D), I],
+        "fcgle_autotune_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,6 +221,15 @@ def fcgle_spectral_scalars(h, func, k, theta, s, flags=0):
     out = (ctypes.c_double * max(1, 2 * n))()
     _check(_lib.fcgle_spectral_scalars(h, func, int(k), float(theta), n, sin, out, int(flags)))
     return [complex(out[2 * j], out[2 * j + 1]) for j in range(n)]
+
+
+def fcgle_autotune_report():
+    """The autotuner's timings and choices so far (one line per tuned shape)."""
+    need = ctypes.c_size_t()
+    _check(_lib.fcgle_autotune_report(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(max(1, need.value))
+    _check(_lib.fcgle_autotune_report(buf, len(buf), None))
+    return buf.value.decode()
 
 
 def fcgle_step(h, scheme, tau, t, u):

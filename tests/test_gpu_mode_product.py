@@ -104,3 +104,37 @@ def test_split_io_equals_fp32_io(fc):
         err = float(torch.linalg.vector_norm(y - Y32) / torch.linalg.vector_norm(Y32))
         assert err <= 1e-5, (mu, err)
     s.close()
+
+
+@pytest.mark.parametrize("ns", [[30, 134, 14], [40, 24, 16], [264, 72], [40]])
+def test_precise_tf32_product_matches_fp64_kernel(fc, ns):
+    """flags bit 2: the precise product of the end transforms (split-TF32 on the
+    tensor cores; FP32 on the CUDA cores for d = 1, where R = 1) against the
+    FP64 kernel.  Split-TF32 keeps about 21 significant bits of each operand
+    (2^-22 relative) and drops lo.lo (below 2^-22); the tensor core's FP32
+    accumulation of the three products over p terms adds the rest.  Measured on
+    GB300: at most 2.4e-6 max-elementwise (p = 264), against 3e-5 for one
+    split-BF16 product; the bound is 5e-6."""
+    s64, _, _ = _solver(fc, ns, "fp64")
+    s32, _, _ = _solver(fc, ns, "bf16x3")
+    P64 = fc.fcgle_internal_elems(s64.h)
+    P32 = fc.fcgle_internal_elems(s32.h)
+    assert P64 == P32                     # sizes chosen so that both layouts pad alike
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    X = torch.randn(2 * P64, device="cuda", dtype=torch.float64, generator=gen)
+    for mu in range(len(ns)):
+        for fwd in (True, False):
+            Y64 = torch.empty_like(X)
+            Y32 = torch.empty(2 * P32, device="cuda", dtype=torch.float32)
+            fc.fcgle_mode_product(s64.h, mu, fwd, X, Y64)
+            fc.fcgle_mode_product(s32.h, mu, int(fwd) | 4, X.float(), Y32)
+            s64.sync()
+            s32.sync()
+            d = Y32.double() - Y64
+            err = max(float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(Y64)),
+                      float(d.abs().max() / Y64.abs().max()))
+            assert err <= 5e-6, (ns, mu, fwd, err)
+    with pytest.raises(fc.FcgleError):
+        fc.fcgle_mode_product(s32.h, 0, 1 | 2 | 4, X.float(), Y32)
+    s64.close()
+    s32.close()
