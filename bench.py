@@ -59,8 +59,9 @@ SCHEME_NAMES = {"krogstad": "Krogstad exponential RK4 (phi_1..phi_3)", "etd2rk":
                 "lawson_rk2": "Lawson-RK2"}
 
 
-def workload_config(n, precision="bf16x3", scheme="krogstad", tau=TAU):
+def workload_config(n, precision="bf16x3", scheme="krogstad", tau=TAU, exp_form="tucker"):
     return {
+        "exp_form": exp_form,
         "workload": f"3D FCGLE {n}^3 on (-10,10)^3, alpha=(1.2,1.5,1.8), nu=1, eta=0.5, gamma=1, kappa=1, "
                     f"zeta=0.5; {SCHEME_NAMES[scheme]}, tau={tau:g}; u0 = Gaussian bump x "
                     f"smoothed random phase (seed 1)",
@@ -375,6 +376,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     solver = fcgle.Solver(ns, BOXES, ALPHAS, **PARS, precision="bf16x3")
+    if args.exp_form != "tucker":
+        solver.set_exp_form(args.exp_form)
     setup_s = time.perf_counter() - t0
     u0_np = inputs.gaussian_random_phase(ns, BOXES, seed=1)
     u0 = torch.from_numpy(u0_np).to(torch.complex64).cuda()
@@ -498,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
         extra["autotune"] = fcgle.fcgle_autotune_report().strip().splitlines()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n, "bf16x3", args.scheme, args.tau),
+                "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n, "bf16x3", args.scheme, args.tau, args.exp_form),
                 "roofline": roofline, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "setup_s": round(setup_s, 3)}
         line.update(extra)
@@ -927,6 +930,9 @@ def main():
     ap.add_argument("--scheme", default="krogstad", choices=sorted(SCHEME_NAMES),
                     help="cube workload: time-stepping scheme (default krogstad, the benchmark)")
     ap.add_argument("--tau", type=float, default=TAU)
+    ap.add_argument("--exp-form", default="tucker", choices=["tucker", "kron"],
+                    help="cube workload, split-BF16: how e^{tau K} is applied by Lawson-Euler, Lawson-RK2 and "
+                         "Strang (Tucker form, or the Kronecker-product form with complex E_mu)")
     ap.add_argument("--workload", default="cube", choices=["cube", "batched", "adjoint", "config2"],
                     help="cube: one 3D n^3 instance (default Krogstad); batched: 96 uneven ETD2RK instances; "
                          "adjoint: gradient of a final-time misfit, 128^3 Lawson-RK2; config2: 2D 1023x1024 LIE "

@@ -147,6 +147,26 @@ fcgle_status fcgle_set_source(fcgle_handle h, int nterms, const double* sigma_re
 fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, double gamma, double kappa,
                                     double zeta);
 
+/* How e^{theta K} is applied (Sec. 3.1-3.2).  FCGLE_EXP_TUCKER: the Tucker
+ * form Q diag(e^{theta lam}) Q^T (Eq. fKu_diag), 2d real mode products.
+ * FCGLE_EXP_KRON: the Kronecker-product form V x_1 E_1 ... x_d E_d with
+ * E_mu = exp(theta A_mu) = Q_mu diag(e^{theta (nu + i eta) lam_mu}) Q_mu^T
+ * (Eqs. Neudecker, Neudeckerd), d complex mode products, half the tensor
+ * traffic.  FP64 handles always use FCGLE_EXP_KRON for the exponential.
+ * BF16X3 handles default to FCGLE_EXP_TUCKER; fcgle_set_exp_form switches
+ * fcgle_apply_f with EXP / PHI k = 0 and the schemes whose only linear
+ * operator is e^{tau K} (LAWSON_EULER, LAWSON_RK2, STRANG) to the Kronecker
+ * form.  Those schemes then carry the physical state u, so the split-BF16
+ * error of every product (about 1e-5 relative) enters the state each step
+ * and accumulates with the step count, whereas the Tucker form carries the
+ * spectral state and lets it enter only through tau-small increments: the
+ * Kronecker form trades accuracy at T for bytes.  E_mu is built in FP64 on
+ * the host once per theta (O(n_mu^3)) and cached until the coefficients
+ * change; batches run the Kronecker form with per-instance launches.  The
+ * adjoint always uses the Tucker form. */
+typedef enum { FCGLE_EXP_TUCKER = 0, FCGLE_EXP_KRON = 1 } fcgle_exp_form;
+fcgle_status fcgle_set_exp_form(fcgle_handle h, int form);
+
 /* out = f(theta K) v with f = 1/(1-z) (func INV), e^z (EXP, Eq. Neudeckerd)
  * or phi_k (PHI, k in 0..4).  v and out are device tensors in the user layout
  * and may alias. */

@@ -946,6 +946,82 @@ struct EpiStrangB {
   }
 };
 
+// ---- Kronecker-product form of the exponential (Eq. Neudeckerd): the state is
+// the physical u (FP32) and each e^{tau K} is d complex mode products.
+
+// Strang: w = e^{tau K} Phi_{tau/2}(u_n) is the product; u_{n+1} = Phi_{tau/2}(w),
+// and the next step's input Phi_{tau/2}(u_{n+1}) = Phi_tau(w) (the flows of the
+// autonomous nonlinear part compose) -> split
+struct EpiStrangKron {
+  FCGLE_EPI(0, 4)
+  uint32_t P;
+  float* U;
+  Flow half, full;
+  SplitOut S;
+  template <int V>
+  __device__ void load(uint32_t, int, uint32_t, float (&)[1][V]) const {}
+  template <int V>
+  __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
+                        const float (&)[1][V]) const {
+    float ur[V], ui[V], sr[V], si[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      flow_eval(half, re[v], im[v], ur[v], ui[v]);
+      flow_eval(full, re[v], im[v], sr[v], si[v]);
+    }
+    stv<V>(U + q, ur);
+    stv<V>(U + P + q, ui);
+    put_csplit<V>(S, P, q, sr, si);
+  }
+};
+
+// Lawson-RK2 (Heun on w = e^{-tK} u): with k_1 = g(t_n, u_n), A = e^{tau K}(u_n + tau k_1)
+// already in FP32, the product is e^{tau K}(u_n + tau/2 k_1) and
+//   u_{n+1} = product + tau/2 g(t_{n+1}, A);
+// the next step's inputs u_{n+1} + tau g(t_{n+1}, u_{n+1}) and u_{n+1} + tau/2 g(...) -> split
+struct EpiLRK2Kron {
+  FCGLE_EPI(2, 2)
+  uint32_t P;
+  const float* A;
+  float* U;
+  GStatic g;
+  GTime t;   // t_{n+1}
+  float tau;
+  SplitOut V1, V2;
+  template <int V>
+  __device__ void load(uint32_t q, int, uint32_t, float (&in)[2][V]) const {
+    ldv<V>(A + q, in[0]);
+    ldv<V>(A + P + q, in[1]);
+  }
+  template <int V>
+  __device__ void store(uint32_t q, int, uint32_t, const float (&re)[V], const float (&im)[V],
+                        const float (&in)[2][V]) const {
+    float gr[V], gi[V], ur[V], ui[V];
+    g_eval<V>(g, t, P, q, in[0], in[1], gr, gi);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      ur[v] = re[v] + 0.5f * tau * gr[v];
+      ui[v] = im[v] + 0.5f * tau * gi[v];
+    }
+    stv<V>(U + q, ur);
+    stv<V>(U + P + q, ui);
+    g_eval<V>(g, t, P, q, ur, ui, gr, gi);
+    float ar[V], ai[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      ar[v] = ur[v] + tau * gr[v];
+      ai[v] = ui[v] + tau * gi[v];
+    }
+    put_csplit<V>(V1, P, q, ar, ai);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      ar[v] = ur[v] + 0.5f * tau * gr[v];
+      ai[v] = ui[v] + 0.5f * tau * gi[v];
+    }
+    put_csplit<V>(V2, P, q, ar, ai);
+  }
+};
+
 #undef FCGLE_EPI
 
 }  // namespace b3

@@ -52,13 +52,19 @@ constexpr uint32_t kEpiWarp = 32 * 33 * 4;
 // of a TMEM lane quarter; an accumulator tile is 4 lane quarters x 4 groups of
 // 16 r columns) and 2 smem stages, which is all the shared memory then leaves.
 // (The plain product, b3_plain.cuh, streams its operands differently.)
-template <class Epi>
+//
+// Complex form (CX = true, the Kronecker-product exponential of Eq. Neudeckerd):
+// M = E = Er + i Ei is complex, so a stage also carries the Ei_hi, Ei_lo
+// chunks (96 KB per stage) and the epilogue drops to 8 warps (two 16-column
+// groups each) to fit the shared memory.
+template <class Epi, bool CX = false>
 struct Cfg {
-  static constexpr int kEpi = 16;
+  static constexpr int kEpi = CX ? 8 : 16;
   static constexpr int kStages = 2;
   static constexpr int kThreads = 32 * (2 + kEpi);
   static constexpr int kGroups = 16 / kEpi;   // 16-column groups per epilogue warp
-  static constexpr uint32_t kOffEpi = kStages * kStage;
+  static constexpr uint32_t kStageBytes = CX ? 3 * kStage / 2 : kStage;
+  static constexpr uint32_t kOffEpi = kStages * kStageBytes;
   static constexpr uint32_t kOffBar = kOffEpi + kEpi * kEpiWarp;
   static constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;   // + barriers + alignment slack
   static_assert(kSmemBytes <= 232448, "shared memory budget");
@@ -74,7 +80,18 @@ struct KParams {
   int k_chunks;     // ceil(p / 64)
   long long tiles;  // ceil(R / 64)
   int* err;
+  int ei_row = 0;   // complex forms: row of Ei in the stacked [Er; Ei] matrix maps
 };
+
+// Complex mode product (Eq. Neudecker): with M = Er + i Ei and the tile's
+// columns 0..63 = re rows, 64..127 = im rows of X,
+//   D[:, 0:64]   = Er Xre - Ei Xim   (re part)
+//   D[:, 64:128] = Er Xim + Ei Xre   (im part)
+// as one N = 128 product with Er over both planes plus two N = 64 products
+// with Ei: negated on the im rows into columns 0..63, plain on the re rows
+// into columns 64..127 (instruction-descriptor bit 13 negates A).  Each of the
+// three is split hi.hi + hi.lo + lo.hi.
+constexpr uint32_t kNegA = 1u << 13;
 
 // -------------------------------------------------------------- PTX helpers
 // Programmatic dependent launch.  Every mode-product kernel lets the next
@@ -211,16 +228,19 @@ struct FusedDesc {
 // Grouped form (G = true): one persistent launch serves the last mode
 // product of several independent problems; maps, sizes and the epilogue
 // functor of problem k come from gd[k].  Same arithmetic per unit.
-template <class Epi, bool G = false>
-__global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
+template <class Epi, bool G = false, bool CX = false>
+__global__ void __launch_bounds__(Cfg<Epi, CX>::kThreads, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                  const KParams kp, const Epi epi, const FusedDesc<Epi>* __restrict__ gd, int ngd,
                  long long gunits) {
-  constexpr int NSTAGE = Cfg<Epi>::kStages;
-  constexpr int NEPI = Cfg<Epi>::kEpi;
-  constexpr uint32_t kOffEpi = Cfg<Epi>::kOffEpi;
-  constexpr uint32_t kOffBar = Cfg<Epi>::kOffBar;
+  static_assert(!(G && CX), "the complex form has no grouped variant");
+  constexpr int NSTAGE = Cfg<Epi, CX>::kStages;
+  constexpr int NEPI = Cfg<Epi, CX>::kEpi;
+  constexpr uint32_t kStg = Cfg<Epi, CX>::kStageBytes;
+  constexpr uint32_t kOffX = CX ? 65536 : 32768;   // X chunks after M (and Ei)
+  constexpr uint32_t kOffEpi = Cfg<Epi, CX>::kOffEpi;
+  constexpr uint32_t kOffBar = Cfg<Epi, CX>::kOffBar;
   extern __shared__ uint8_t smem_raw[];
   pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -298,14 +318,18 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
           const int s = (int)(g % NSTAGE);
           const uint32_t ph = (g / NSTAGE) & 1;
           if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1)) { ok = false; break; }
-          const uint32_t st = sbase + s * kStage;
-          mbar_arrive_tx(full_bar(s), kStage);
+          const uint32_t st = sbase + s * kStg;
+          mbar_arrive_tx(full_bar(s), kStg);
           tma_load_2d(st, mmh, kc * BK, mb * BM, full_bar(s));
           tma_load_2d(st + 16384, mml, kc * BK, mb * BM, full_bar(s));
-          tma_load_2d(st + 32768, mxh, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + 32768 + 8192, mxh, kc * BK, r1, full_bar(s));
-          tma_load_2d(st + 49152, mxl, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + 49152 + 8192, mxl, kc * BK, r1, full_bar(s));
+          if constexpr (CX) {
+            tma_load_2d(st + 32768, mmh, kc * BK, kp.ei_row + mb * BM, full_bar(s));
+            tma_load_2d(st + 49152, mml, kc * BK, kp.ei_row + mb * BM, full_bar(s));
+          }
+          tma_load_2d(st + kOffX, mxh, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + kOffX + 8192, mxh, kc * BK, r1, full_bar(s));
+          tma_load_2d(st + kOffX + 16384, mxl, kc * BK, r0, full_bar(s));
+          tma_load_2d(st + kOffX + 16384 + 8192, mxl, kc * BK, r1, full_bar(s));
         }
       }
       // drain: every issued stage must have landed before the CTA may exit
@@ -318,6 +342,8 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                  ((uint32_t)(BM >> 4) << 24);
+      constexpr uint32_t idesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BR >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
       bool ok = true;
       int pid = 0;
@@ -336,8 +362,8 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
           const uint32_t ph = (g / NSTAGE) & 1;
           if (!mbar_wait(full_bar(s), ph, abort_flag, err, 3)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ahi = sbase + s * kStage, alo = ahi + 16384;
-          const uint32_t bhi = ahi + 32768, blo = ahi + 49152;
+          const uint32_t ahi = sbase + s * kStg, alo = ahi + 16384;
+          const uint32_t bhi = ahi + kOffX, blo = bhi + 16384;
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint32_t off = ks * 32;
@@ -345,6 +371,16 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
             mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
             mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
             mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+            if constexpr (CX) {
+              // Ei chunks at +32 KB (hi) and +48 KB (lo); X re rows at bhi, im rows at bhi + 8 KB
+              const uint32_t eh = ahi + 32768, el = ahi + 49152;
+              mma_bf16(d_tmem, sw128_desc(eh + off), sw128_desc(bhi + 8192 + off), idesc64 | kNegA, 1u);
+              mma_bf16(d_tmem, sw128_desc(eh + off), sw128_desc(blo + 8192 + off), idesc64 | kNegA, 1u);
+              mma_bf16(d_tmem, sw128_desc(el + off), sw128_desc(bhi + 8192 + off), idesc64 | kNegA, 1u);
+              mma_bf16(d_tmem + BR, sw128_desc(eh + off), sw128_desc(bhi + off), idesc64, 1u);
+              mma_bf16(d_tmem + BR, sw128_desc(eh + off), sw128_desc(blo + off), idesc64, 1u);
+              mma_bf16(d_tmem + BR, sw128_desc(el + off), sw128_desc(bhi + off), idesc64, 1u);
+            }
           }
           mma_commit(empty_bar(s));
         }
@@ -383,7 +419,7 @@ __global__ void __launch_bounds__(Cfg<Epi>::kThreads, 1)
       const int i_base = mb * BM + q * 32;
       // all of this warp's accumulator columns into registers, then hand the
       // accumulator back to the MMA warp before any store or functor work
-      constexpr int NG = Cfg<Epi>::kGroups;
+      constexpr int NG = Cfg<Epi, CX>::kGroups;
       uint32_t vr[NG][16], vi[NG][16];
 #pragma unroll
       for (int g2 = 0; g2 < NG; ++g2) {

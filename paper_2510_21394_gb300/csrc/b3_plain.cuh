@@ -106,20 +106,25 @@ constexpr int kMaxRing = 4;       // barrier slots per ring
 //   NXR = 4: X 4 x 32 KB + M 2 x 32 KB (the default, and the grouped form)
 //   NXR = 3: X 3 + M 3;  NXR = 2: X 2 + M 4 (long k extents: more M in flight)
 //   MR:      X 2 + resident M (p <= 256)
-template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false>
+//   CX:      the complex (Kronecker-product exponential) form: M = Er + i Ei,
+//            an M stage carries Er_hi, Er_lo, Ei_hi, Ei_lo (64 KB); X 2 + M 2
+//            (the products are those of the complex fused form, b3_kernel.cuh)
+template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false, bool CX = false>
 __global__ void __launch_bounds__(PL_THREADS, 1)
     mp_b3_plain_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                        const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                        const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                        const KParams kp, const PlainDesc* __restrict__ gd, int ngd, long long gunits) {
-  static_assert(!(G && (MR || NXR != PL_NX)), "the grouped form uses the default rings");
+  static_assert(!(G && (MR || CX || NXR != PL_NX)), "the grouped form uses the default rings");
+  static_assert(!(CX && (MR || OP != kOpBF16)), "the complex form is split-BF16 with M rings");
   // X ring depth and the offset of the M region (ring or resident); the
   // epilogue staging area starts at the same offset in every configuration
-  constexpr int NX = MR ? 2 : NXR;
-  constexpr int NM = MR ? kMRMaxChunks : (int)((kPlOffEpi - NX * kXStage) / kMStage);
+  constexpr uint32_t kMSt = CX ? 2 * kMStage : kMStage;   // bytes per M stage
+  constexpr int NX = (MR || CX) ? 2 : NXR;
+  constexpr int NM = MR ? kMRMaxChunks : (int)((kPlOffEpi - NX * kXStage) / kMSt);
   constexpr uint32_t kOffM = NX * kXStage;
   static_assert(NX >= 2 && NX <= kMaxRing && NM >= 2 && NM <= kMaxRing, "ring depths");
-  static_assert(kOffM + NM * kMStage == kPlOffEpi, "shared memory layout");
+  static_assert(kOffM + NM * kMSt == kPlOffEpi, "shared memory layout");
   extern __shared__ uint8_t smem_raw[];
   pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -245,11 +250,15 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % NM);
           if (!mbar_wait(empty_m(s), ((g / NM) & 1) ^ 1, abort_flag, err, 12)) { ok = false; break; }
-          const uint32_t st = sbase + kOffM + s * kMStage;
-          mbar_arrive_tx(full_m(s), kMStage);
+          const uint32_t st = sbase + kOffM + s * kMSt;
+          mbar_arrive_tx(full_m(s), kMSt);
           constexpr int CK = chunk_k<OP>();
           tma_load_2d(st, mmh, kc * CK, mb * BM, full_m(s));
           tma_load_2d(st + 16384, mml, kc * CK, mb * BM, full_m(s));
+          if constexpr (CX) {
+            tma_load_2d(st + 32768, mmh, kc * CK, kp.ei_row + mb * BM, full_m(s));
+            tma_load_2d(st + 49152, mml, kc * CK, kp.ei_row + mb * BM, full_m(s));
+          }
         }
       }
       const uint32_t issued = g;
@@ -263,6 +272,8 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       constexpr uint32_t kAB = OP == kOpBF16 ? 1u : 2u;
       constexpr uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(BN >> 3) << 17) |
                                  ((uint32_t)(BM >> 4) << 24);
+      constexpr uint32_t idesc64 = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(BR >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
       bool ok = true;
       int pid = 0;
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
           if (!MR && !mbar_wait(full_m(sm), (g / NM) & 1, abort_flag, err, 14)) { ok = false; break; }
           if (!mbar_wait(full_x(sx), (g / NX) & 1, abort_flag, err, 15)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ahi = sbase + kOffM + sm * kMStage, alo = ahi + 16384;
+          const uint32_t ahi = sbase + kOffM + sm * kMSt, alo = ahi + 16384;
           const uint32_t bhi = sbase + sx * kXStage, blo = bhi + 16384;
           // four k-steps of 32 bytes per 128-byte row (K = 16 bf16 or 8 tf32 each)
 #pragma unroll
@@ -293,6 +304,15 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
               mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
               mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
               mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+              if constexpr (CX) {
+                const uint32_t eh = ahi + 32768, el = ahi + 49152;
+                mma_bf16(d_tmem, sw128_desc(eh + off), sw128_desc(bhi + 8192 + off), idesc64 | kNegA, 1u);
+                mma_bf16(d_tmem, sw128_desc(eh + off), sw128_desc(blo + 8192 + off), idesc64 | kNegA, 1u);
+                mma_bf16(d_tmem, sw128_desc(el + off), sw128_desc(bhi + 8192 + off), idesc64 | kNegA, 1u);
+                mma_bf16(d_tmem + BR, sw128_desc(eh + off), sw128_desc(bhi + off), idesc64, 1u);
+                mma_bf16(d_tmem + BR, sw128_desc(eh + off), sw128_desc(blo + off), idesc64, 1u);
+                mma_bf16(d_tmem + BR, sw128_desc(el + off), sw128_desc(bhi + off), idesc64, 1u);
+              }
             } else {
               mma_tf32(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
               mma_tf32(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);

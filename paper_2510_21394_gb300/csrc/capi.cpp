@@ -198,6 +198,14 @@ fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, doubl
   });
 }
 
+fcgle_status fcgle_set_exp_form(fcgle_handle h, int form) {
+  return guarded([&] {
+    check_handle(h);
+    h->eng->set_exp_form(form);
+    ++h->gen;
+  });
+}
+
 fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta, const void* v, void* out) {
   return guarded([&] {
     check_handle(h);

@@ -41,6 +41,11 @@ class EngineBase {
   virtual void set_source(int nterms, const double* sig, const void* const* S_user) = 0;
   // new nu, eta, gamma, kappa, zeta (the eigendecompositions do not depend on them)
   virtual void set_coefficients(double nu, double eta, double gamma, double kappa, double zeta) = 0;
+  // how e^{theta K} is applied (fcgle_exp_form); FP64 engines always use the
+  // Kronecker-product form and only validate the value
+  virtual void set_exp_form(int form) {
+    if (form != FCGLE_EXP_TUCKER && form != FCGLE_EXP_KRON) throw InvalidArg("unknown exponential form");
+  }
   virtual void apply_f(int func, int k, double theta, const void* v, void* out) = 0;
   virtual void step(int scheme, double tau, double t, void* u) = 0;
   virtual void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;

@@ -276,6 +276,18 @@ __global__ void flow_kernel(uint32_t P, b3::Flow f, const float* __restrict__ W,
   }
 }
 
+// V = Phi_t(u) -> split (Strang's first half step, Kronecker-product form)
+__global__ void flow_split_kernel(uint32_t P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    float ur[4], ui[4], vr[4], vi[4];
+    b3::ldv<4>(U + q, ur);
+    b3::ldv<4>(U + P + q, ui);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) b3::flow_eval(f, ur[v], ui[v], vr[v], vi[v]);
+    b3::put_csplit<4>(V, P, q, vr, vi);
+  }
+}
+
 // V = Phi_t(u) - u -> split (Strang's first half step as an increment)
 __global__ void flow_incr_split_kernel(uint32_t P, b3::Flow f, const float* __restrict__ U, SplitOut V) {
   for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
@@ -360,6 +372,7 @@ class EngineB3 : public EngineBase {
     for (int mu = 0; mu < prm.d; ++mu) {
       Direction D = spectral_direction(prm, mu);
       h_[mu] = D.h;
+      dir_[mu] = D;   // Q_mu, lam_mu kept for the exponential matrices E_mu
       std::vector<float> lf(s_.p[mu], 0.f);
       std::vector<double> ld(s_.p[mu], 0.0);
       for (int j = 0; j < D.n; ++j) {
@@ -423,6 +436,13 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiLRK2A>();
       set_smem_attr<b3::EpiLRK2B>();
       set_smem_attr<b3::EpiStrangB>();
+      set_smem_attr_cx<b3::EpiStoreF32>();
+      set_smem_attr_cx<b3::EpiStoreSplitGen>();
+      set_smem_attr_cx<b3::EpiUpdateG>();
+      set_smem_attr_cx<b3::EpiStrangKron>();
+      set_smem_attr_cx<b3::EpiLRK2Kron>();
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b3::kPlSmemBytes));
       FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)b3::kPlSmemBytes));
       for (int c = 0; c < kNumPlainCfg; ++c)
@@ -473,6 +493,13 @@ class EngineB3 : public EngineBase {
     gs_.gamma = (float)gamma;
     gs_.kappa = (float)kappa;
     gs_.zeta = (float)zeta;
+    FCGLE_CUDA(cudaStreamSynchronize(st_));   // cached E_mu may still be in use
+    ecache_.clear();
+  }
+
+  void set_exp_form(int form) override {
+    if (form != FCGLE_EXP_TUCKER && form != FCGLE_EXP_KRON) throw InvalidArg("unknown exponential form");
+    exp_form_ = form;
   }
 
   void spectral_scalars(int func, int k, double theta, int count, const double* s_host, double* out_host,
@@ -539,6 +566,12 @@ class EngineB3 : public EngineBase {
     pack_f32((const float*)v, X);
     SplitOut V = SP(kV);
     gsplit(X, 0.0, 1.f, 0.f, V);
+    if (func == FCGLE_F_EXP && kron()) {
+      // Eq. Neudeckerd: d complex mode products instead of two Tucker operators
+      exp_kron(V, theta, b3::EpiStoreF32{P32(), X});
+      unpack_f32(X, (float*)out, true);
+      return;
+    }
     tucker(V, true, b3::EpiScaleF{P32(), lf_, fkind(func, k), (float)theta, V});
     tucker(V, false, b3::EpiStoreF32{P32(), X});
     unpack_f32(X, (float*)out, true);
@@ -659,6 +692,155 @@ class EngineB3 : public EngineBase {
   static void set_smem_attr() {
     FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)b3::Cfg<Epi>::kSmemBytes));
+  }
+  template <class Epi>
+  static void set_smem_attr_cx() {
+    FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)b3::Cfg<Epi, true>::kSmemBytes));
+  }
+
+  // ---- Kronecker-product form of the exponential (Eq. Neudeckerd)
+  // E_mu = exp(theta A_mu) = Q_mu diag(e^{theta (nu + i eta) lam}) Q_mu^T, complex
+  // symmetric; as a mode-product operand the real and imaginary parts are
+  // stacked, [Er; Ei] ((2 m_pad) x k_pad), and split into bf16 hi + lo.
+  struct CMat {
+    __nv_bfloat16* hi = nullptr;
+    __nv_bfloat16* lo = nullptr;
+    int m_pad = 0, k_pad = 0;
+    CUtensorMap tm_hi, tm_lo;
+    CMat() = default;
+    CMat(const CMat&) = delete;
+    CMat& operator=(const CMat&) = delete;
+    ~CMat() {
+      if (hi) cudaFree(hi);
+      if (lo) cudaFree(lo);
+    }
+  };
+
+  // E_mu for every direction at theta, built once (FP64 on the host) and cached
+  // until the coefficients change
+  const std::vector<std::unique_ptr<CMat>>& emat(double theta) {
+    uint64_t key;
+    std::memcpy(&key, &theta, 8);
+    auto it = ecache_.find(key);
+    if (it != ecache_.end()) return it->second;
+    auto& v = ecache_[key];
+    for (int mu = 0; mu < s_.d; ++mu) {
+      const Direction& D = dir_[mu];
+      const int n = D.n, p = s_.p[mu];
+      std::vector<double> er(n), ei(n);
+      for (int j = 0; j < n; ++j) {
+        const double m = std::exp(theta * prm_.nu * D.lam[j]);
+        er[j] = m * std::cos(theta * prm_.eta * D.lam[j]);
+        ei[j] = m * std::sin(theta * prm_.eta * D.lam[j]);
+      }
+      std::unique_ptr<CMat> c(new CMat);
+      c->m_pad = (p + b3::BM - 1) / b3::BM * b3::BM;
+      c->k_pad = (p + b3::BK - 1) / b3::BK * b3::BK;
+      const size_t rows = 2 * (size_t)c->m_pad, K = (size_t)c->k_pad;
+      std::vector<__nv_bfloat16> hi(rows * K, __float2bfloat16(0.0f)), lo(hi);
+      auto put = [&](size_t row, int k, double x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+        hi[row * K + k] = h;
+        lo[row * K + k] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+      };
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k <= i; ++k) {
+          double sr = 0.0, si = 0.0;
+          const double* qi = &D.Q[(size_t)i * n];
+          const double* qk = &D.Q[(size_t)k * n];
+          for (int j = 0; j < n; ++j) {
+            const double w = qi[j] * qk[j];
+            sr += w * er[j];
+            si += w * ei[j];
+          }
+          put((size_t)i, k, sr);
+          put((size_t)k, i, sr);
+          put((size_t)c->m_pad + i, k, si);
+          put((size_t)c->m_pad + k, i, si);
+        }
+      const size_t bytes = hi.size() * 2;
+      FCGLE_CUDA(cudaMalloc(&c->hi, bytes));
+      FCGLE_CUDA(cudaMalloc(&c->lo, bytes));
+      FCGLE_CUDA(cudaMemcpy(c->hi, hi.data(), bytes, cudaMemcpyHostToDevice));
+      FCGLE_CUDA(cudaMemcpy(c->lo, lo.data(), bytes, cudaMemcpyHostToDevice));
+      encode_bf16(&c->tm_hi, c->hi, (uint64_t)c->k_pad, rows, b3::BM);
+      encode_bf16(&c->tm_lo, c->lo, (uint64_t)c->k_pad, rows, b3::BM);
+      v.push_back(std::move(c));
+    }
+    return v;
+  }
+
+  b3::KParams kparams_cx(int mu, const CMat& c) const {
+    b3::KParams kp;
+    kp.R = P_ / s_.p[mu];
+    kp.p = s_.p[mu];
+    kp.m_blocks = c.m_pad / b3::BM;
+    kp.k_chunks = c.k_pad / b3::BK;
+    kp.tiles = (kp.R + b3::BR - 1) / b3::BR;
+    kp.err = err_->ptr;
+    kp.ei_row = c.m_pad;
+    return kp;
+  }
+
+  // one complex mode product with epilogue (fused kernel, complex form)
+  template <class Epi>
+  void launch_mp_cx(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, const CMat& c, const Epi& epi) {
+    const b3::KParams kp = kparams_cx(mu, c);
+    CUtensorMap txh, txl;
+    encode_bf16(&txh, xh, (uint64_t)s_.p[mu], 2 * (uint64_t)kp.R, b3::BR);
+    encode_bf16(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)kp.R, b3::BR);
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    launch_pdl(b3::mp_b3_kernel<Epi, false, true>, grid, b3::Cfg<Epi, true>::kThreads,
+               b3::Cfg<Epi, true>::kSmemBytes, st_, txh, txl, c.tm_hi, c.tm_lo, kp, epi,
+               (const b3::FusedDesc<Epi>*)nullptr, 0, 0LL);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  // one complex mode product with a split output
+  void store_split_cx(const __nv_bfloat16* xh, const __nv_bfloat16* xl, int mu, const CMat& c, SplitOut out) {
+    const b3::KParams kp = kparams_cx(mu, c);
+    if (kp.R % 8 != 0) {
+      launch_mp_cx(xh, xl, mu, c, b3::EpiStoreSplitGen{P32(), out});
+      return;
+    }
+    CUtensorMap txh, txl, tyh, tyl;
+    encode_bf16(&txh, xh, (uint64_t)s_.p[mu], 2 * (uint64_t)kp.R, b3::BR);
+    encode_bf16(&txl, xl, (uint64_t)s_.p[mu], 2 * (uint64_t)kp.R, b3::BR);
+    encode_bf16_out(&tyh, out.hi, (uint64_t)kp.R, (uint64_t)s_.p[mu]);
+    encode_bf16_out(&tyl, out.lo, (uint64_t)kp.R, (uint64_t)s_.p[mu]);
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    launch_pdl(b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, false, true>, grid, b3::PL_THREADS, b3::kPlSmemBytes,
+               st_, txh, txl, c.tm_hi, c.tm_lo, tyh, tyl, kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  // e^{theta K} applied to the split tensor `in` (consumed) as V x_1 E_1 ... x_d E_d;
+  // the last product runs `epi` (which may write into `in` for d >= 2)
+  template <class Epi>
+  void exp_kron(SplitOut in, double theta, const Epi& epi) {
+    const auto& E = emat(theta);
+    const int d = s_.d;
+    SplitOut src = in;
+    if (d == 1) {
+      SplitOut t = SP(kT1);
+      FCGLE_CUDA(cudaMemcpyAsync(t.hi, in.hi, 4 * s_.P * 2, cudaMemcpyDeviceToDevice, st_));
+      src = t;
+    }
+    for (int mu = 0; mu < d - 1; ++mu) {
+      SplitOut dst = SP(mu % 2 == 0 ? kT0 : kT1);
+      store_split_cx(src.hi, src.lo, mu, *E[mu], dst);
+      src = dst;
+    }
+    launch_mp_cx(src.hi, src.lo, d - 1, *E[d - 1], epi);
+  }
+
+  bool kron() const { return exp_form_ == FCGLE_EXP_KRON; }
+  // schemes whose only operator is e^{tau K}, run in the Kronecker-product form when chosen
+  bool kron_scheme(int scheme) const {
+    return kron() && (scheme == FCGLE_LAWSON_EULER || scheme == FCGLE_LAWSON_RK2 || scheme == FCGLE_STRANG);
   }
 
   void prepare_matrix(const double* M, int p, Mat& m) {
@@ -1074,6 +1256,7 @@ class EngineB3 : public EngineBase {
   // u(T) from the carried spectral state by the FP32 backward operator (Strang:
   // u(T) = Phi_{tau/2}(bwd(e^))), replacing the split-BF16 one of the last step
   void finish() {
+    if (kron_scheme(rs_scheme_)) return;   // the physical state is already in F32(kU)
     if (rs_scheme_ == FCGLE_STRANG) {
       float* W = F32(kWork);
       tucker_f32(F32(kUh), W, false);
@@ -1092,6 +1275,19 @@ class EngineB3 : public EngineBase {
     float* U = F32(kU);
     SplitOut V = SP(kV);
     const float ft = (float)tau;
+    if (kron_scheme(scheme)) {
+      // Kronecker-product form: the state is the physical u; V (and W) = the
+      // input of the first e^{tau K} of step 0
+      if (scheme == FCGLE_STRANG) {
+        flow_split_kernel<<<grid_for(P_ / 4), 256, 0, st_>>>(P32(), flow(tau / 2), U, V);
+        FCGLE_LAUNCHED(launches);
+      } else if (scheme == FCGLE_LAWSON_EULER) {
+        gsplit(U, t0, 1.f, ft, V);
+      } else {
+        gsplit(U, t0, 1.f, ft, V, 1.f, 0.5f * ft, SP(kW));
+      }
+      return;
+    }
     switch (scheme) {
       case FCGLE_STRANG:
         // e^_0 = fwd(u_0) (FP32); V = Phi_{tau/2}(u_0) - u_0
@@ -1120,6 +1316,21 @@ class EngineB3 : public EngineBase {
     float* U = F32(kU);
     SplitOut V = SP(kV);
     const float ft = (float)tau;
+    if (kron_scheme(scheme)) {
+      if (scheme == FCGLE_LAWSON_EULER) {
+        // u_{n+1} = e^{tau K}(u_n + tau g_n);  V = u_{n+1} + tau g(t_{n+1}, u_{n+1})
+        exp_kron(V, tau, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t + tau), 1.f, ft, V});
+      } else if (scheme == FCGLE_STRANG) {
+        // w = e^{tau K} Phi_{tau/2}(u_n);  u_{n+1} = Phi_{tau/2}(w);  V = Phi_tau(w)
+        exp_kron(V, tau, b3::EpiStrangKron{P32(), U, flow(tau / 2), flow(tau), V});
+      } else {
+        // A = e^{tau K}(u_n + tau k_1);  u_{n+1} = e^{tau K}(u_n + tau/2 k_1) + tau/2 g(t_{n+1}, A)
+        SplitOut W = SP(kW);
+        exp_kron(V, tau, b3::EpiStoreF32{P32(), F32(kEA)});
+        exp_kron(W, tau, b3::EpiLRK2Kron{P32(), F32(kEA), U, gs_, gtime(t + tau), ft, V, W});
+      }
+      return;
+    }
     switch (scheme) {
       case FCGLE_LIE:
       case FCGLE_LAWSON_EULER: {
@@ -1203,6 +1414,7 @@ class EngineB3 : public EngineBase {
   bool time_dependent() const override { return gs_.nsrc > 0; }
   bool set_recorder(std::vector<GroupRec>* rec) override {
     if (rec && s_.d < 2) return false;   // d == 1 copies the input aside inside a Tucker operator
+    if (rec && kron_scheme(rs_scheme_)) return false;   // the complex products have no grouped form
     rec_ = rec;
     return true;
   }
@@ -1229,6 +1441,9 @@ class EngineB3 : public EngineBase {
   std::unique_ptr<DevMem<float>> src_[kMaxSrc];
   std::unique_ptr<DevMem<float>> host_stage_;
   std::unique_ptr<DevMem<float>> tsp_[2];   // split-TF32 work tensors of the precise transforms
+  Direction dir_[kMaxDim];
+  int exp_form_ = FCGLE_EXP_TUCKER;
+  std::map<uint64_t, std::vector<std::unique_ptr<CMat>>> ecache_;
   std::unique_ptr<DevMem<double>> scratch_;
   std::unique_ptr<DevMem<int>> err_;
 };

@@ -28,6 +28,10 @@ FCGLE_FP64 = 0
 FCGLE_TF32 = 1      # not built: fcgle_setup answers FCGLE_ERR_UNSUPPORTED
 FCGLE_BF16X3 = 2
 
+FCGLE_EXP_TUCKER = 0
+FCGLE_EXP_KRON = 1
+EXP_FORMS = {"tucker": FCGLE_EXP_TUCKER, "kron": FCGLE_EXP_KRON}
+
 FCGLE_F_INV = 0
 FCGLE_F_EXP = 1
 FCGLE_F_PHI = 2
@@ -43,7 +47,7 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
            "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait", "fcgle_spectral_scalars",
-           "fcgle_autotune_report"]
+           "fcgle_autotune_report", "fcgle_set_exp_form"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -94,6 +98,7 @@ def _load():
         "fcgle_selftest_bounded_wait": [P, ctypes.POINTER(I)],
         "fcgle_spectral_scalars": [H, I, I, D, I, ctypes.POINTER(D), ctypes.POINTER(D), I],
         "fcgle_autotune_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+        "fcgle_set_exp_form": [H, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -204,6 +209,11 @@ def fcgle_set_source(h, sigmas, tensors):
 
 def fcgle_set_coefficients(h, nu, eta, gamma, kappa, zeta):
     _check(_lib.fcgle_set_coefficients(h, float(nu), float(eta), float(gamma), float(kappa), float(zeta)))
+
+
+def fcgle_set_exp_form(h, form):
+    form = EXP_FORMS[form] if isinstance(form, str) else int(form)
+    _check(_lib.fcgle_set_exp_form(h, form))
 
 
 def fcgle_apply_f(h, func, k, theta, v, out):
@@ -383,6 +393,10 @@ class Solver:
 
     def set_coefficients(self, nu, eta, gamma, kappa, zeta):
         fcgle_set_coefficients(self.h, nu, eta, gamma, kappa, zeta)
+
+    def set_exp_form(self, form):
+        """'tucker' (default for bf16x3) or 'kron' (Kronecker-product form of e^{tau K})."""
+        fcgle_set_exp_form(self.h, form)
 
     def apply_f(self, func, k, theta, v, out=None):
         v = self._check_tensor(v.contiguous())
