@@ -307,7 +307,9 @@ fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P);
  * the precise product used for the first and last Tucker operators of a time
  * integration, FP32 in and out: split-TF32 (x = hi + lo, both TF32, three
  * tensor-core products hi.hi + hi.lo + lo.hi, about 2^-21 relative) when
- * d >= 2 and R is a multiple of 8, FP32 on the CUDA cores otherwise.  Other
+ * d >= 2, R is a multiple of 8 and p_mu <= 256 (the tensor core's FP32
+ * accumulation error grows with the contracted length), FP32 on the CUDA
+ * cores otherwise.  Other
  * flag bits give FCGLE_ERR_INVALID_ARG.  X and Y must not overlap.  direction
  * in 0..d-1. */
 fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y);

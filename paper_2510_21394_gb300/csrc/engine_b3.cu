@@ -534,7 +534,7 @@ class EngineB3 : public EngineBase {
       // the precise form of the end transforms: FP32 planar in and out
       if (flags & 2) throw InvalidArg("flags bits 1 and 2 exclude each other");
       const long long R = P_ / s_.p[mu];
-      if (s_.d >= 2 && R % 8 == 0) {
+      if (s_.d >= 2 && R % 8 == 0 && s_.p[mu] <= kTf32MaxP) {
         for (int k = 0; k < 2; ++k)
           if (!tsp_[k]) tsp_[k].reset(new DevMem<float>(4 * s_.P));
         float* A = tsp_[0]->ptr;
@@ -636,7 +636,7 @@ class EngineB3 : public EngineBase {
     FCGLE_LAUNCHED(launches);
     tucker(V, fwd, b3::EpiStoreF32{P32(), Y});
   }
-  void tuckerT_precise(const float* X, float* Y, bool fwd) { tucker_f32(X, Y, fwd); }
+  void tuckerT_precise(const float* X, float* Y, bool fwd) { tucker_f32(X, Y, fwd, false); }
 
   void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
                void* grad_u0, double* grad_params, double* loss) override {
@@ -888,11 +888,16 @@ class EngineB3 : public EngineBase {
   // split-BF16 error must not enter: U^_0 = fwd(u_0) at the start of a time
   // integration and u(T) = bwd(U^_T) at its end.  Split-TF32 on the tensor
   // cores (about 2^-21 relative per product) when every output row pitch
-  // allows the FP32 TMA boxes (d >= 2, R % 8 == 0); FP32 on the CUDA cores
-  // otherwise.
-  void tucker_f32(const float* X, float* Y, bool fwd) {
-    bool tc = s_.d >= 2;
-    for (int mu = 0; mu < s_.d && tc; ++mu) tc = (P_ / s_.p[mu]) % 8 == 0;
+  // allows the FP32 TMA boxes (d >= 2, R % 8 == 0) and every contraction is at
+  // most kTf32MaxP long: the tensor core's FP32 accumulation of the three
+  // products adds an error that grows with the contracted length (measured
+  // 2.4e-6 at p = 264; at p = 1024 it lifted the error at T of 500 steps from
+  // 1.6e-6 to 8.5e-6).  FP32 on the CUDA cores otherwise, and always when
+  // tc_ok is false (the adjoint, whose misfit compares nearby states).
+  static constexpr int kTf32MaxP = 256;
+  void tucker_f32(const float* X, float* Y, bool fwd, bool tc_ok = true) {
+    bool tc = tc_ok && s_.d >= 2;
+    for (int mu = 0; mu < s_.d && tc; ++mu) tc = (P_ / s_.p[mu]) % 8 == 0 && s_.p[mu] <= kTf32MaxP;
     if (tc) {
       tucker_tf32(X, Y, fwd);
       return;
@@ -1080,6 +1085,8 @@ class EngineB3 : public EngineBase {
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      // another configuration replaces the default only when it is clearly faster
+      if (e.cfg != kCfgX4M2 && e.us[kCfgX4M2] > 0.f && e.us[e.cfg] > 0.98f * e.us[kCfgX4M2]) e.cfg = kCfgX4M2;
       if (device_error()) throw DeviceTimeout("a bounded device-side wait gave up while tuning the mode product");
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune.emplace(std::make_tuple(s_.p[mu], R), e);

@@ -109,12 +109,13 @@ def test_split_io_equals_fp32_io(fc):
 @pytest.mark.parametrize("ns", [[30, 134, 14], [40, 24, 16], [264, 72], [40]])
 def test_precise_tf32_product_matches_fp64_kernel(fc, ns):
     """flags bit 2: the precise product of the end transforms (split-TF32 on the
-    tensor cores; FP32 on the CUDA cores for d = 1, where R = 1) against the
-    FP64 kernel.  Split-TF32 keeps about 21 significant bits of each operand
+    tensor cores for p <= 256; FP32 on the CUDA cores for d = 1, where R = 1,
+    and for p = 264) against the FP64 kernel.  Split-TF32 keeps about 21 significant bits of each operand
     (2^-22 relative) and drops lo.lo (below 2^-22); the tensor core's FP32
     accumulation of the three products over p terms adds the rest.  Measured on
-    GB300: at most 2.4e-6 max-elementwise (p = 264), against 3e-5 for one
-    split-BF16 product; the bound is 5e-6."""
+    GB300: at most 2.4e-6 max-elementwise (p = 264, before that size moved to
+    the CUDA cores), against 3e-5 for one split-BF16 product; the bound is
+    5e-6."""
     s64, _, _ = _solver(fc, ns, "fp64")
     s32, _, _ = _solver(fc, ns, "bf16x3")
     P64 = fc.fcgle_internal_elems(s64.h)
