@@ -792,6 +792,7 @@ def run_batched(args, rank, world, local_rank):
                      "unit": "GB/s", "frac": round(step_gbs / (peak * world), 4),
                      "floor_ms": round(step_bytes / (peak * world * 1e9) * 1e3, 4),
                      "peak_kind": f"{peak_kind} hbm_gbs (burst) x {world} GPU(s)"}
+        tune = [ln for ln in fcgle.fcgle_autotune_report().strip().splitlines() if ln.startswith("batch phase")]
         line = {"metric": METRIC, "value": dof_all * args.steps / (r["ms"] / 1e3), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "bf16x3",
@@ -807,7 +808,7 @@ def run_batched(args, rank, world, local_rank):
                 "graph_of_per_instance_launches": {
                     "value": dof_all * args.steps / (res["graph"]["ms"] / 1e3),
                     "ms_per_step": res["graph"]["ms"] / args.steps},
-                "setup_s": round(setup_s, 2)}
+                "setup_s": round(setup_s, 2), "autotune_phases": tune}
         print(json.dumps(line))
     return 0
 

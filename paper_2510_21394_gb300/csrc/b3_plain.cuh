@@ -101,30 +101,36 @@ __device__ __forceinline__ float tf32_round(float x) {
 constexpr int kMRMaxChunks = 4;   // resident M: up to 4 chunks of 32 KB
 constexpr int kMaxRing = 4;       // barrier slots per ring
 
-// Ring configurations of the single form (X ring depth NXR; the M ring takes
-// the rest of the 192 KB operand area, or the resident region when MR):
+// Ring configurations (X ring depth NXR; the M ring takes the rest of the
+// 192 KB operand area, or the resident region when MR, single form only):
 //   NXR = 4: X 4 x 32 KB + M 2 x 32 KB (the default, and the grouped form)
 //   NXR = 3: X 3 + M 3;  NXR = 2: X 2 + M 4 (long k extents: more M in flight)
 //   MR:      X 2 + resident M (p <= 256)
+//   MH:      X 3 + resident M_hi (4 x 16 KB) + M_lo ring 2 x 16 KB (p <= 256):
+//            a third less operand traffic per unit than streaming M, one X
+//            stage more than MR
 //   CX:      the complex (Kronecker-product exponential) form: M = Er + i Ei,
 //            an M stage carries Er_hi, Er_lo, Ei_hi, Ei_lo (64 KB); X 2 + M 2
 //            (the products are those of the complex fused form, b3_kernel.cuh)
-template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false, bool CX = false>
+template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false, bool CX = false, bool MH = false>
 __global__ void __launch_bounds__(PL_THREADS, 1)
     mp_b3_plain_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                        const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                        const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                        const KParams kp, const PlainDesc* __restrict__ gd, int ngd, long long gunits) {
-  static_assert(!(G && (MR || CX || NXR != PL_NX)), "the grouped form uses the default rings");
-  static_assert(!(CX && (MR || OP != kOpBF16)), "the complex form is split-BF16 with M rings");
+  static_assert(!(G && (MR || CX || MH)), "the grouped form streams M through a ring");
+  static_assert(!(CX && (MR || MH || OP != kOpBF16)), "the complex form is split-BF16 with M rings");
+  static_assert(!(MH && (MR || OP != kOpBF16)), "resident M_hi is a split-BF16 form of its own");
   // X ring depth and the offset of the M region (ring or resident); the
   // epilogue staging area starts at the same offset in every configuration
-  constexpr uint32_t kMSt = CX ? 2 * kMStage : kMStage;   // bytes per M stage
-  constexpr int NX = (MR || CX) ? 2 : NXR;
-  constexpr int NM = MR ? kMRMaxChunks : (int)((kPlOffEpi - NX * kXStage) / kMSt);
+  constexpr uint32_t kHalf = kMStage / 2;                 // one 128 x 64 bf16 box (hi or lo)
+  constexpr uint32_t kMSt = CX ? 2 * kMStage : (MH ? kHalf : kMStage);   // bytes per M ring stage
+  constexpr int NX = (MR || CX) ? 2 : (MH ? 3 : NXR);
+  constexpr int NM = MR ? kMRMaxChunks : (MH ? 2 : (int)((kPlOffEpi - NX * kXStage) / kMSt));
   constexpr uint32_t kOffM = NX * kXStage;
-  static_assert(NX >= 2 && NX <= kMaxRing && NM >= 2 && NM <= kMaxRing, "ring depths");
-  static_assert(kOffM + NM * kMSt == kPlOffEpi, "shared memory layout");
+  constexpr uint32_t kOffMlo = kOffM + kMRMaxChunks * kHalf;   // MH: the M_lo ring after the resident M_hi
+  static_assert(NX >= 2 && NX <= kMaxRing && NM >= 2 && NM <= kMaxRing - (MH ? 1 : 0), "ring depths");
+  static_assert((MH ? kOffMlo : kOffM) + NM * kMSt == kPlOffEpi, "shared memory layout");
   extern __shared__ uint8_t smem_raw[];
   pdl_trigger();
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -235,6 +241,14 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       uint32_t g = 0;
       bool ok = true;
       int pid = 0;
+      if (MH && (long long)blockIdx.x < units) {
+        // the CTA's fixed i-block of M_hi, all k-chunks, loaded once (barrier slot 3)
+        const int mb = (int)(blockIdx.x % kp.m_blocks);
+        constexpr int CK = chunk_k<OP>();
+        mbar_arrive_tx(full_m(kMaxRing - 1), (uint32_t)kp.k_chunks * kHalf);
+        for (int kc = 0; kc < kp.k_chunks; ++kc)
+          tma_load_2d(sbase + kOffM + kc * kHalf, &tm_mhi, kc * CK, mb * BM, full_m(kMaxRing - 1));
+      }
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
         long long lu = u;
         int mbk = kp.m_blocks, KC = kp.k_chunks;
@@ -250,9 +264,15 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % NM);
           if (!mbar_wait(empty_m(s), ((g / NM) & 1) ^ 1, abort_flag, err, 12)) { ok = false; break; }
+          constexpr int CK = chunk_k<OP>();
+          if constexpr (MH) {   // the M_lo ring only
+            const uint32_t st = sbase + kOffMlo + s * kMSt;
+            mbar_arrive_tx(full_m(s), kMSt);
+            tma_load_2d(st, mml, kc * CK, mb * BM, full_m(s));
+            continue;
+          }
           const uint32_t st = sbase + kOffM + s * kMSt;
           mbar_arrive_tx(full_m(s), kMSt);
-          constexpr int CK = chunk_k<OP>();
           tma_load_2d(st, mmh, kc * CK, mb * BM, full_m(s));
           tma_load_2d(st + 16384, mml, kc * CK, mb * BM, full_m(s));
           if constexpr (CX) {
@@ -264,6 +284,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       const uint32_t issued = g;
       for (uint32_t q = issued >= (uint32_t)NM ? issued - NM : 0; q < issued; ++q)
         mbar_wait(full_m(q % NM), (q / NM) & 1, abort_flag, err, 18, true);
+      if (MH && (long long)blockIdx.x < units) mbar_wait(full_m(kMaxRing - 1), 0, abort_flag, err, 18, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -278,6 +299,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       bool ok = true;
       int pid = 0;
       if (MR && (long long)blockIdx.x < units) ok = mbar_wait(full_m(0), 0, abort_flag, err, 14);
+      if (MH && (long long)blockIdx.x < units) ok = mbar_wait(full_m(kMaxRing - 1), 0, abort_flag, err, 14);
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
         int KC = kp.k_chunks;
         if constexpr (G) {
@@ -293,7 +315,8 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
           if (!MR && !mbar_wait(full_m(sm), (g / NM) & 1, abort_flag, err, 14)) { ok = false; break; }
           if (!mbar_wait(full_x(sx), (g / NX) & 1, abort_flag, err, 15)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ahi = sbase + kOffM + sm * kMSt, alo = ahi + 16384;
+          const uint32_t ahi = MH ? sbase + kOffM + kc * kHalf : sbase + kOffM + sm * kMSt;
+          const uint32_t alo = MH ? sbase + kOffMlo + sm * kMSt : ahi + 16384;
           const uint32_t bhi = sbase + sx * kXStage, blo = bhi + 16384;
           // four k-steps of 32 bytes per 128-byte row (K = 16 bf16 or 8 tf32 each)
 #pragma unroll

@@ -45,6 +45,8 @@ struct fcgle_batch_ctx {
     size_t offset;     // of its descriptor array in dev
     int n;
     long long units;
+    std::vector<void (*)(const void*, int, long long, cudaStream_t)> alts;   // equivalent configurations
+    std::vector<std::string> alt_names;
   };
   struct Plan {
     std::vector<Phase> phases;
@@ -488,6 +490,8 @@ fcgle_status fcgle_batch_instance(fcgle_batch b, int i, fcgle_handle* h) {
   });
 }
 
+static void tune_plan(fcgle_batch_ctx::Plan& plan, cudaStream_t st);
+
 // Record step `n` of every instance and group the records into phases: for
 // each Tucker operator of the step, the k-th inner mode product of all
 // instances (k = 0, 1, ..), then the last mode products; records of one phase
@@ -531,7 +535,7 @@ static bool build_plan(fcgle_batch_ctx* b, int n, cudaStream_t st, fcgle_batch_c
     for (auto* r : rs)
       if (std::find(kinds.begin(), kinds.end(), r->launch) == kinds.end()) kinds.push_back(r->launch);
     for (auto fn : kinds) {
-      fcgle_batch_ctx::Phase ph{fn, (host.size() + 255) / 256 * 256, 0, 0};
+      fcgle_batch_ctx::Phase ph{fn, (host.size() + 255) / 256 * 256, 0, 0, {}, {}};
       host.resize(ph.offset);
       for (auto* r : rs) {
         if (r->launch != fn) continue;
@@ -540,6 +544,8 @@ static bool build_plan(fcgle_batch_ctx* b, int n, cudaStream_t st, fcgle_batch_c
         std::memcpy(host.data() + at + r->ubegin_off, &ph.units, sizeof(long long));
         ph.units += r->units;
         ++ph.n;
+        ph.alts = r->alts;
+        ph.alt_names = r->alt_names;
       }
       plan.phases.push_back(ph);
     }
@@ -561,7 +567,60 @@ static bool build_plan(fcgle_batch_ctx* b, int n, cudaStream_t st, fcgle_batch_c
   FCGLE_CUDA(cudaMalloc(&plan.dev, std::max<size_t>(host.size(), 256)));
   FCGLE_CUDA(cudaMemcpyAsync(plan.dev, host.data(), host.size(), cudaMemcpyHostToDevice, st));
   FCGLE_CUDA(cudaStreamSynchronize(st));
+  tune_plan(plan, st);
   return true;
+}
+
+// Per-phase autotuning of a grouped plan: a phase whose kernel has equivalent
+// configurations (the plain mode product's ring depths) is timed in each, on
+// the batch's own buffers, and the fastest is kept (another configuration
+// replaces the recorded one only when 2 % faster).  Plain phases read the
+// step's input and write only the scratch tensors of their Tucker operator, so
+// running them out of order before the step changes no state.  Synchronous;
+// the choices are added to the autotuner's report.
+static void tune_plan(fcgle_batch_ctx::Plan& plan, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  FCGLE_CUDA(cudaEventCreate(&e0));
+  FCGLE_CUDA(cudaEventCreate(&e1));
+  int k = 0;
+  try {
+    for (auto& ph : plan.phases) {
+      ++k;
+      if (ph.alts.empty()) continue;
+      const void* d = static_cast<const uint8_t*>(plan.dev) + ph.offset;
+      std::vector<void (*)(const void*, int, long long, cudaStream_t)> cands = {ph.launch};
+      cands.insert(cands.end(), ph.alts.begin(), ph.alts.end());
+      std::vector<float> us(cands.size(), 0.f);
+      for (size_t c = 0; c < cands.size(); ++c) {
+        cands[c](d, ph.n, ph.units, st);   // warm-up
+        FCGLE_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) cands[c](d, ph.n, ph.units, st);
+        FCGLE_CUDA(cudaEventRecord(e1, st));
+        FCGLE_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FCGLE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        us[c] = 1e3f * ms / 3;
+      }
+      size_t best = 0;
+      for (size_t c = 1; c < cands.size(); ++c)
+        if (us[c] < 0.98f * us[0] && us[c] < us[best]) best = c;
+      char line[320];
+      int n = std::snprintf(line, sizeof(line), "batch phase %d (%d instances, %lld units): X4M2 %.1fus", k, ph.n,
+                            ph.units, us[0]);
+      for (size_t c = 1; c < cands.size() && n > 0 && n < (int)sizeof(line); ++c)
+        n += std::snprintf(line + n, sizeof(line) - n, " %s %.1fus", ph.alt_names[c - 1].c_str(), us[c]);
+      if (n > 0 && n < (int)sizeof(line))
+        std::snprintf(line + n, sizeof(line) - n, " -> %s", best == 0 ? "X4M2" : ph.alt_names[best - 1].c_str());
+      add_tune_report_line(line);
+      ph.launch = cands[best];
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 fcgle_status fcgle_batch_integrate(fcgle_batch b, int scheme, double tau, int nsteps, double t0,

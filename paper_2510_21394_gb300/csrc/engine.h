@@ -93,6 +93,10 @@ class EngineBase {
 struct GroupRec {
   bool last;   // last mode product of a Tucker operator (carries the scheme's epilogue)
   void (*launch)(const void* descs, int n, long long units, cudaStream_t st);
+  // launchers of equivalent kernel configurations that read the same descriptor
+  // format (the autotuner of a batch times them per phase); may be empty
+  std::vector<void (*)(const void*, int, long long, cudaStream_t)> alts;
+  std::vector<std::string> alt_names;
   size_t ubegin_off;          // byte offset of the descriptor's first-unit field
   std::vector<uint8_t> desc;  // the descriptor bytes (size = stride in the array)
   long long units;
@@ -104,7 +108,9 @@ Direction spectral_direction(const fcgle_params& prm, int mu);
 
 std::unique_ptr<EngineBase> make_engine(const fcgle_params& prm, cudaStream_t st);
 // the plain-product autotuner's timings and choices so far, one line per shape
+// (and one per tuned phase of a batch)
 std::string plain_tune_report();
+void add_tune_report_line(const std::string& line);
 std::unique_ptr<EngineBase> make_engine_b3(const fcgle_params& prm, cudaStream_t st);
 
 }  // namespace fcgle

@@ -87,8 +87,8 @@ void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaSt
 // (all eligible configurations, on the handle's own work buffers, at setup) and
 // the fastest is used from then on.  FCGLE_PLAIN_CFG=<id> (read once) forces
 // one configuration where it is eligible.
-enum PlainCfg { kCfgX4M2 = 0, kCfgX3M3 = 1, kCfgX2M4 = 2, kCfgMR = 3, kNumPlainCfg = 4 };
-const char* const kPlainCfgName[kNumPlainCfg] = {"X4M2", "X3M3", "X2M4", "residentM"};
+enum PlainCfg { kCfgX4M2 = 0, kCfgX3M3 = 1, kCfgX2M4 = 2, kCfgMR = 3, kCfgMH = 4, kNumPlainCfg = 5 };
+const char* const kPlainCfgName[kNumPlainCfg] = {"X4M2", "X3M3", "X2M4", "residentM", "residentMhi"};
 
 using PlainKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
                              b3::KParams, const b3::PlainDesc*, int, long long);
@@ -98,6 +98,7 @@ PlainKernel plain_kernel(int cfg) {
     case kCfgX3M3: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 3>;
     case kCfgX2M4: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2>;
     case kCfgMR: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, true>;
+    case kCfgMH: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 3, false, false, true>;
     default: return b3::mp_b3_plain_kernel<false>;
   }
 }
@@ -114,7 +115,7 @@ int forced_plain_cfg() {
 
 struct TuneEntry {
   int cfg = kCfgX4M2;
-  float us[kNumPlainCfg] = {-1.f, -1.f, -1.f, -1.f};   // -1: not eligible
+  float us[kNumPlainCfg] = {-1.f, -1.f, -1.f, -1.f, -1.f};   // -1: not eligible
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, long long>, TuneEntry> g_tune;   // (p, R)
@@ -129,10 +130,18 @@ bool tuned_lookup(int p, long long R, TuneEntry& e) {
 
 }  // namespace
 
+static std::vector<std::string> g_tune_lines;   // tuned phases of batches
+
+void add_tune_report_line(const std::string& line) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_lines.push_back(line);
+}
+
 // Text report of the autotuner's choices (C ABI: fcgle_autotune_report).
 std::string plain_tune_report() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   std::string out;
+  for (const auto& l : g_tune_lines) out += l + "\n";
   char line[256];
   for (const auto& kv : g_tune) {
     int n = std::snprintf(line, sizeof(line), "plain p=%d R=%lld:", std::get<0>(kv.first), std::get<1>(kv.first));
@@ -997,7 +1006,9 @@ class EngineB3 : public EngineBase {
       d.yhi = tyh;
       d.ylo = tyl;
       d.kp = kp;
-      record(false, &launch_plain_grouped, offsetof(b3::PlainDesc, ubegin), &d, sizeof(d), units);
+      record(false, &launch_plain_grouped<b3::PL_NX>, offsetof(b3::PlainDesc, ubegin), &d, sizeof(d), units);
+      rec_->back().alts = {&launch_plain_grouped<3>, &launch_plain_grouped<2>};
+      rec_->back().alt_names = {kPlainCfgName[kCfgX3M3], kPlainCfgName[kCfgX2M4]};
       return;
     }
     int cfg = forced_plain_cfg();
@@ -1015,15 +1026,14 @@ class EngineB3 : public EngineBase {
     return units < sms ? (int)units : sms - sms % m_blocks;
   }
   static bool plain_cfg_ok(int cfg, const b3::KParams& kp, long long units) {
-    if (cfg != kCfgMR) return true;
+    if (cfg != kCfgMR && cfg != kCfgMH) return true;
     return kp.k_chunks <= b3::kMRMaxChunks && grid_mr(units, kp.m_blocks) >= kp.m_blocks;
   }
-  static int default_plain_cfg(const b3::KParams& kp, long long units) {
-    return plain_cfg_ok(kCfgMR, kp, units) ? kCfgMR : kCfgX4M2;
-  }
+  static int default_plain_cfg(const b3::KParams&, long long) { return kCfgX4M2; }
   void launch_plain_cfg(int cfg, const CUtensorMap& txh, const CUtensorMap& txl, const Mat& m, const CUtensorMap& tyh,
                         const CUtensorMap& tyl, const b3::KParams& kp, long long units) {
-    const int grid = cfg == kCfgMR ? grid_mr(units, kp.m_blocks) : (int)std::min<long long>(units, num_sms());
+    const int grid = (cfg == kCfgMR || cfg == kCfgMH) ? grid_mr(units, kp.m_blocks)
+                                                       : (int)std::min<long long>(units, num_sms());
     launch_pdl(plain_kernel(cfg), grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl, m.tm_hi, m.tm_lo, tyh, tyl,
                kp, (const b3::PlainDesc*)nullptr, 0, 0LL);
     FCGLE_LAUNCHED(launches);
@@ -1106,18 +1116,19 @@ class EngineB3 : public EngineBase {
     r.units = units;
     rec_->push_back(std::move(r));
   }
+  template <int NXR>
   static void launch_plain_grouped(const void* descs, int n, long long units, cudaStream_t st) {
     static std::once_flag attr;
     std::call_once(attr, [] {
-      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)b3::kPlSmemBytes));
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_plain_kernel<true, b3::kOpBF16, NXR>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b3::kPlSmemBytes));
     });
     CUtensorMap z;
     std::memset(&z, 0, sizeof(z));
     b3::KParams kp{};
     const int grid = (int)std::min<long long>(units, num_sms());
-    launch_pdl(b3::mp_b3_plain_kernel<true>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st, z, z, z, z, z, z, kp,
-               static_cast<const b3::PlainDesc*>(descs), n, units);
+    launch_pdl(b3::mp_b3_plain_kernel<true, b3::kOpBF16, NXR>, grid, b3::PL_THREADS, b3::kPlSmemBytes, st, z, z, z, z,
+               z, z, kp, static_cast<const b3::PlainDesc*>(descs), n, units);
   }
   template <class Epi>
   static void launch_fused_grouped(const void* descs, int n, long long units, cudaStream_t st) {

@@ -60,46 +60,97 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 }
 
 // ----------------------------------------------------------------- pack
-// One thread per internal element (all P of them, padding included).
+// One thread per 4 consecutive internal elements of a row of direction 1 (all
+// P of them, padding included: p_1 is a multiple of 4), so that the index
+// arithmetic is one division per 4 elements and the planar stores are 4-wide.
+// Row rho = j_2 + p_2 j_3 of the internal layout holds user row
+// (j_2 + n_2 j_3) when j_2 < n_2 and j_3 < n_3.
+struct RowMap {
+  size_t user_row;   // first user element of the row (valid rows)
+  bool valid;
+};
+__device__ __forceinline__ RowMap row_map(const Shape& s, size_t rho) {
+  RowMap m{0, true};
+  if (s.d >= 2) {
+    const int j2 = (int)(rho % (size_t)s.p[1]);
+    const int j3 = (int)(rho / (size_t)s.p[1]);
+    m.valid = j2 < s.n[1] && j3 < s.n[2];
+    m.user_row = ((size_t)j2 + (size_t)s.n[1] * (size_t)j3) * (size_t)s.n[0];
+  }
+  return m;
+}
+
 template <typename T>
 __global__ void pack_kernel(Shape s, const T* __restrict__ user, T* __restrict__ X) {
-  const size_t P = s.P;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
-    size_t rem = q;
-    int j[kMaxDim] = {0, 0, 0};
-    bool valid = true;
-    for (int mu = 0; mu < s.d; ++mu) {
-      j[mu] = (int)(rem % s.p[mu]);
-      rem /= s.p[mu];
-      valid = valid && j[mu] < s.n[mu];
+  const size_t P = s.P, quads_per_row = (size_t)s.p[0] / 4, nq = P / 4;
+  const int n1 = s.n[0];
+  for (size_t q4 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q4 < nq; q4 += (size_t)gridDim.x * blockDim.x) {
+    const size_t rho = q4 / quads_per_row;
+    const int j1 = (int)(q4 - rho * quads_per_row) * 4;
+    const RowMap m = row_map(s, rho);
+    T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+    if (m.valid) {
+      const T* src = user + 2 * (m.user_row + (size_t)j1);
+      if (j1 + 4 <= n1 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 a = reinterpret_cast<const float4*>(src)[0], b = reinterpret_cast<const float4*>(src)[1];
+          re[0] = a.x; im[0] = a.y; re[1] = a.z; im[1] = a.w;
+          re[2] = b.x; im[2] = b.y; re[3] = b.z; im[3] = b.w;
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const double2 a = reinterpret_cast<const double2*>(src)[v];
+            re[v] = a.x;
+            im[v] = a.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (j1 + v < n1) {
+            re[v] = src[2 * v];
+            im[v] = src[2 * v + 1];
+          }
+      }
     }
-    T re = 0, im = 0;
-    if (valid) {
-      size_t u = (size_t)j[0] + (size_t)s.n[0] * ((size_t)j[1] + (size_t)s.n[1] * (size_t)j[2]);
-      re = user[2 * u];
-      im = user[2 * u + 1];
-    }
-    X[q] = re;
-    X[P + q] = im;
+    st4<T>(X + 4 * q4, re);
+    st4<T>(X + P + 4 * q4, im);
   }
 }
 
 template <typename T>
 __global__ void unpack_kernel(Shape s, const T* __restrict__ X, T* __restrict__ user, int* __restrict__ nonfinite) {
-  const size_t N = s.N;
+  const size_t P = s.P, quads_per_row = (size_t)s.p[0] / 4, nq = P / 4;
+  const int n1 = s.n[0];
   bool bad = false;
-  for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < N; u += (size_t)gridDim.x * blockDim.x) {
-    size_t rem = u, q = 0, stride = 1;
-    for (int mu = 0; mu < s.d; ++mu) {
-      int j = (int)(rem % s.n[mu]);
-      rem /= s.n[mu];
-      q += (size_t)j * stride;
-      stride *= s.p[mu];
+  for (size_t q4 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q4 < nq; q4 += (size_t)gridDim.x * blockDim.x) {
+    const size_t rho = q4 / quads_per_row;
+    const int j1 = (int)(q4 - rho * quads_per_row) * 4;
+    const RowMap m = row_map(s, rho);
+    if (!m.valid || j1 >= n1) continue;
+    T re[4], im[4];
+    ld4<T>(X + 4 * q4, re);
+    ld4<T>(X + P + 4 * q4, im);
+    T* dst = user + 2 * (m.user_row + (size_t)j1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) bad |= (j1 + v < n1) && !(isfinite(re[v]) && isfinite(im[v]));
+    if (j1 + 4 <= n1 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      // 4 whole complex values, 16-byte aligned: vector stores of (re, im) pairs
+      if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(re[0], im[0], re[1], im[1]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(re[2], im[2], re[3], im[3]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) reinterpret_cast<double2*>(dst)[v] = make_double2(re[v], im[v]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (j1 + v < n1) {
+          dst[2 * v] = re[v];
+          dst[2 * v + 1] = im[v];
+        }
     }
-    const T re = X[q], im = X[s.P + q];
-    user[2 * u] = re;
-    user[2 * u + 1] = im;
-    bad |= !(isfinite(re) && isfinite(im));
   }
   // a non-finite entry is recorded unless an earlier device error is already there
   if (bad && nonfinite) atomicCAS(nonfinite, 0, kErrNonFinite);
@@ -395,12 +446,12 @@ LamDev lamdev(const Shape& s, const LamVecs& lv) {
 // ===================================================================== host
 template <typename T>
 void pack(const Shape& s, const T* user, T* X, cudaStream_t st, long long& nl) {
-  pack_kernel<T><<<grid_for(s.P, 256), 256, 0, st>>>(s, user, X);
+  pack_kernel<T><<<grid_for(s.P / 4, 256), 256, 0, st>>>(s, user, X);
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
 void unpack(const Shape& s, const T* X, T* user, cudaStream_t st, long long& nl, int* nonfinite) {
-  unpack_kernel<T><<<grid_for(s.N, 256), 256, 0, st>>>(s, X, user, nonfinite);
+  unpack_kernel<T><<<grid_for(s.P / 4, 256), 256, 0, st>>>(s, X, user, nonfinite);
   FCGLE_LAUNCHED(nl);
 }
 
