@@ -96,3 +96,40 @@ def test_large_mode_sizes(fc):
         s.sync()
         assert rel(got, tensor.Spectral(P).apply_f("phi", 1, 0.01, V)) <= TOL_APPLY
         s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+def test_zero_steps_return_the_input(fc, prec):
+    """nsteps = 0 is the identity on the state (pack then unpack, no step)."""
+    ns, boxes, al = SMALL_CASES[4]
+    dt = torch.complex64 if prec == "bf16x3" else torch.complex128
+    s = fc.Solver(ns, boxes, al, **PARS, precision=prec)
+    u0 = torch.from_numpy(rand_tensor(ns, 8)).to(dt).cuda()
+    for scheme in ("krogstad", "lbdf2", "strang"):
+        out = s.integrate(scheme, 1e-3, 0, u0)
+        s.sync()
+        assert torch.equal(out, u0)
+    s.close()
+
+
+def test_large_extents_many_blocks_and_chunks(fc):
+    """2D 2048 x 1536: 16 and 12 i-blocks, 32 and 24 k-chunks per unit; the
+    plain product runs in the autotuner's choice for these shapes, and the
+    precise end transforms on the CUDA cores (p > 256)."""
+    ns = [2048, 1536]
+    boxes = [(-20.0, 20.0), (-15.0, 15.0)]
+    al = [1.3, 1.7]
+    P = tensor.Problem(ns, boxes, al, *PARS.values())
+    S = tensor.Spectral(P)
+    V = rand_tensor(ns, 12).astype(np.complex64).astype(np.complex128)
+    s = fc.Solver(ns, boxes, al, **PARS, precision="bf16x3")
+    for func, k in (("phi", 1), ("inv", 0)):
+        got = _host(s.apply_f(func, k, 1e-3, _dev(V)))
+        assert rel(got, S.apply_f(func, k, 1e-3, V)) <= TOL_APPLY
+    u0 = (0.8 * inputs.gaussian_pulse(ns, boxes)).astype(np.complex64).astype(np.complex128)
+    g = schemes.Nonlinearity(P)
+    ref = schemes.integrate(S, g, "etd2rk", 1e-3, 2, u0)
+    got = _host(s.integrate("etd2rk", 1e-3, 2, _dev(u0)))
+    s.sync()
+    assert rel(got, ref) <= TOL_INTEGRATE
+    s.close()
