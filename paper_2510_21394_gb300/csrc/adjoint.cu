@@ -172,20 +172,42 @@ __global__ void axpby_kernel(size_t n, double a, const T* __restrict__ x1, doubl
 }
 
 // ---- FP32 forms (split-BF16 engine): per-element arithmetic in FP32 with
-// 32-bit indices (2 P < 2^32 there), reductions still accumulated in FP64.
-__device__ __forceinline__ bool lam_sum32(const LD& L, uint32_t q, float& s) {
-  double acc = 0.0;
-  bool valid = true;
-  uint32_t rem = q;
-  for (int mu = 0; mu < L.d; ++mu) {
+// 32-bit indices (2 P < 2^32 there), 4 consecutive elements of a row of
+// direction 1 per thread step (p_1 is a multiple of 8), 16-byte accesses;
+// reductions are summed in FP32 over a thread's few elements and accumulated
+// in FP64 across threads and blocks.
+struct Quad {
+  float s[4];      // eigenvalue sums (without the factor nu + i eta)
+  bool valid[4];   // interior (not padding)
+};
+// the 4 elements q .. q + 3 (q % 4 == 0, all in one row of direction 1)
+__device__ __forceinline__ Quad quad_lam(const LD& L, uint32_t q) {
+  Quad o;
+  const uint32_t p1 = (uint32_t)L.p[0];
+  const uint32_t j1 = q % p1;
+  uint32_t rem = q / p1;
+  float base = 0.f;
+  bool ok = true;
+  for (int mu = 1; mu < L.d; ++mu) {
     const uint32_t p = (uint32_t)L.p[mu];
     const uint32_t j = rem % p;
     rem /= p;
-    valid = valid && (int)j < L.n[mu];
-    acc += L.lam[mu][j];
+    ok = ok && (int)j < L.n[mu];
+    base += (float)L.lam[mu][j];
   }
-  s = (float)acc;
-  return valid;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    o.valid[v] = ok && (int)(j1 + v) < L.n[0];
+    o.s[v] = base + (float)L.lam[0][j1 + v];
+  }
+  return o;
+}
+__device__ __forceinline__ void ld4f(const float* p, float (&v)[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void st4f(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 __device__ __forceinline__ void gadj_f(float gam, float kap, float zet, float zr, float zi, float wr, float wi,
@@ -197,26 +219,33 @@ __device__ __forceinline__ void gadj_f(float gam, float kap, float zet, float zr
   orr = ar * wr + ai * wi + br * wr + bi * wi;
   oi = ar * wi - ai * wr + bi * wr - br * wi;
 }
-__device__ __forceinline__ void gpar_f(float zr, float zi, float wr, float wi, double (&v)[3]) {
-  const float m2 = zr * zr + zi * zi;
-  const float d = wr * zr + wi * zi, e = wr * (-zi) + wi * zr;
-  v[0] += (double)d;
-  v[1] += (double)(-m2 * d);
-  v[2] += (double)(-m2 * e);
-}
 
 __global__ void gv_kernel_f(uint32_t P, GP g, const float* __restrict__ z, const float* __restrict__ w, float c,
                             float* __restrict__ mu, double* acc) {
-  double v[3] = {0.0, 0.0, 0.0};
+  float f[3] = {0.f, 0.f, 0.f};
   const float gam = (float)g.gamma, kap = (float)g.kappa, zet = (float)g.zeta;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-    const float zr = z[q], zi = z[P + q], wr = c * w[q], wi = c * w[P + q];
-    float orr, oi;
-    gadj_f(gam, kap, zet, zr, zi, wr, wi, orr, oi);
-    mu[q] = orr;
-    mu[P + q] = oi;
-    gpar_f(zr, zi, wr, wi, v);
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    float zr[4], zi[4], wr[4], wi[4], orr[4], oi[4];
+    ld4f(z + q, zr);
+    ld4f(z + P + q, zi);
+    ld4f(w + q, wr);
+    ld4f(w + P + q, wi);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      wr[v] *= c;
+      wi[v] *= c;
+      gadj_f(gam, kap, zet, zr[v], zi[v], wr[v], wi[v], orr[v], oi[v]);
+      // Re<w, dg/dp(z)> for p = gamma, kappa, zeta
+      const float m2 = zr[v] * zr[v] + zi[v] * zi[v];
+      const float dd = wr[v] * zr[v] + wi[v] * zi[v], ee = wi[v] * zr[v] - wr[v] * zi[v];
+      f[0] += dd;
+      f[1] -= m2 * dd;
+      f[2] -= m2 * ee;
+    }
+    st4f(mu + q, orr);
+    st4f(mu + P + q, oi);
   }
+  double v[3] = {(double)f[0], (double)f[1], (double)f[2]};
   block_acc<3>(v, acc, ADJ_GAMMA);
 }
 
@@ -226,42 +255,62 @@ __global__ void gv_kernel_f(uint32_t P, GP g, const float* __restrict__ z, const
 // sweeps apply again every step.  Padding (j >= n) gives y = 0.
 __global__ void scale_exp_kernel_f(uint32_t P, LD L, float ar, float ai, const float* __restrict__ x,
                                    float* __restrict__ y) {
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-    float s;
-    const bool valid = lam_sum32(L, q, s);
-    float mr = -1.f, mi = 0.f;
-    if (valid) {
-      const float a = ar * s, b = ai * s;
-      float sn, cs, sh, ch;
-      sincosf(b, &sn, &cs);
-      sincosf(0.5f * b, &sh, &ch);
-      const float em = expm1f(a);
-      mr = em * cs - 2.f * sh * sh;
-      mi = (1.f + em) * sn;
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    const Quad Q = quad_lam(L, q);
+    float xr[4], xi[4], yr[4], yi[4];
+    ld4f(x + q, xr);
+    ld4f(x + P + q, xi);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float mr = -1.f, mi = 0.f;
+      if (Q.valid[v]) {
+        const float a = ar * Q.s[v], b = ai * Q.s[v];
+        float sn, cs, sh, ch;
+        sincosf(b, &sn, &cs);
+        sincosf(0.5f * b, &sh, &ch);
+        const float em = expm1f(a);
+        mr = em * cs - 2.f * sh * sh;
+        mi = (1.f + em) * sn;
+      }
+      yr[v] = xr[v] + (mr * xr[v] - mi * xi[v]);
+      yi[v] = xi[v] + (mr * xi[v] + mi * xr[v]);
     }
-    const float xr = x[q], xi = x[P + q];
-    y[q] = xr + (mr * xr - mi * xi);
-    y[P + q] = xi + (mr * xi + mi * xr);
+    st4f(y + q, yr);
+    st4f(y + P + q, yi);
   }
 }
 
 __global__ void spec_dot_kernel_f(uint32_t P, LD L, const float* __restrict__ x, const float* __restrict__ y,
                                   double* acc) {
-  double v[2] = {0.0, 0.0};
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-    float s;
-    if (!lam_sum32(L, q, s)) continue;
-    const float xr = x[q], xi = x[P + q], yr = y[q], yi = y[P + q];
-    v[0] += (double)(s * (xr * yr + xi * yi));
-    v[1] += (double)(s * (xr * yi - xi * yr));
+  float f[2] = {0.f, 0.f};
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    const Quad Q = quad_lam(L, q);
+    float xr[4], xi[4], yr[4], yi[4];
+    ld4f(x + q, xr);
+    ld4f(x + P + q, xi);
+    ld4f(y + q, yr);
+    ld4f(y + P + q, yi);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (!Q.valid[v]) continue;
+      f[0] += Q.s[v] * (xr[v] * yr[v] + xi[v] * yi[v]);   // Re conj(x) y
+      f[1] += Q.s[v] * (xr[v] * yi[v] - xi[v] * yr[v]);   // Im conj(x) y
+    }
   }
+  double v[2] = {(double)f[0], (double)f[1]};
   block_acc<2>(v, acc, ADJ_Z_RE);
 }
 
 __global__ void axpby_kernel_f(uint32_t n, float a, const float* __restrict__ x1, float b,
                                const float* __restrict__ x2, float* __restrict__ y) {
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-    y[q] = x2 ? a * x1[q] + b * x2[q] : a * x1[q];
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < n; q += 4 * gridDim.x * blockDim.x) {
+    float u[4], w[4] = {0.f, 0.f, 0.f, 0.f};
+    ld4f(x1 + q, u);
+    if (x2) ld4f(x2 + q, w);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) u[v] = a * u[v] + b * w[v];
+    st4f(y + q, u);
+  }
 }
 
 LD make_ld(const Shape& s, const LamVecs& lv) {
@@ -286,8 +335,8 @@ template <typename T>
 void adj_gv(const Shape& s, const GParams& gp, const T* z, const T* w, double c, T* mu, double* acc, cudaStream_t st,
             long long& nl) {
   if constexpr (std::is_same<T, float>::value)
-    gv_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, (float)c, mu,
-                                               acc);
+    gv_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, (float)c,
+                                                   mu, acc);
   else
     gv_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, GP{gp.gamma, gp.kappa, gp.zeta}, z, w, c, mu, acc);
   FCGLE_LAUNCHED(nl);
@@ -302,7 +351,7 @@ template <typename T>
 void adj_scale_exp(const Shape& s, const LamVecs& lv, double theta, bool conj, const T* x, T* y, cudaStream_t st,
                    long long& nl) {
   if constexpr (std::is_same<T, float>::value)
-    scale_exp_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
+    scale_exp_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
                                                       (float)((conj ? -1.0 : 1.0) * theta * lv.c_im), x, y);
   else
     scale_exp_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re,
@@ -313,7 +362,7 @@ template <typename T>
 void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, double* acc, cudaStream_t st,
                   long long& nl) {
   if constexpr (std::is_same<T, float>::value)
-    spec_dot_kernel_f<<<grid_of(s.P), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), x, y, acc);
+    spec_dot_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), x, y, acc);
   else
     spec_dot_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), x, y, acc);
   FCGLE_LAUNCHED(nl);
@@ -321,7 +370,7 @@ void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, dou
 template <typename T>
 void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* y, cudaStream_t st, long long& nl) {
   if constexpr (std::is_same<T, float>::value)
-    axpby_kernel_f<<<grid_of(2 * s.P), 256, 0, st>>>((uint32_t)(2 * s.P), (float)a, x1, (float)b, x2, y);
+    axpby_kernel_f<<<grid_of(2 * s.P / 4), 256, 0, st>>>((uint32_t)(2 * s.P), (float)a, x1, (float)b, x2, y);
   else
     axpby_kernel<T><<<grid_of(2 * s.P), 256, 0, st>>>(2 * s.P, a, x1, b, x2, y);
   FCGLE_LAUNCHED(nl);

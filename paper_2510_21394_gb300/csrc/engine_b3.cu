@@ -544,12 +544,10 @@ class EngineB3 : public EngineBase {
       if (flags & 2) throw InvalidArg("flags bits 1 and 2 exclude each other");
       const long long R = P_ / s_.p[mu];
       if (s_.d >= 2 && R % 8 == 0 && s_.p[mu] <= kTf32MaxP) {
-        for (int k = 0; k < 2; ++k)
-          if (!tsp_[k]) tsp_[k].reset(new DevMem<float>(4 * s_.P));
-        float* A = tsp_[0]->ptr;
-        tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), (const float*)X, A, A + 2 * s_.P);
+        float *ah = F32(kFh), *al = F32(kD2);   // work tensors of the schemes, free here
+        tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), (const float*)X, ah, al);
         FCGLE_LAUNCHED(launches);
-        launch_tf32(A, A + 2 * s_.P, mu, fwd, (float*)Y, nullptr);
+        launch_tf32(ah, al, mu, fwd, (float*)Y, nullptr);
       } else {
         mp_f32((const float*)X, (float*)Y, mat_[mu][fwd ? 0 : 1].f32, s_.p[mu], (size_t)R, st_, launches);
       }
@@ -914,19 +912,20 @@ class EngineB3 : public EngineBase {
     tucker_simt(X, Y, fwd);
   }
 
+  // The split-TF32 intermediates (hi and lo, 2 P floats each) live in four of
+  // the schemes' FP32 work tensors, which hold nothing at the two ends of a
+  // time integration where this runs (X and Y are the state tensors U, U^ or
+  // the Strang work tensor, never these four).
   void tucker_tf32(const float* X, float* Y, bool fwd) {
-    for (int k = 0; k < 2; ++k)
-      if (!tsp_[k]) tsp_[k].reset(new DevMem<float>(4 * s_.P));   // hi planes (2 P), then lo planes (2 P)
-    float* A = tsp_[0]->ptr;
-    float* B = tsp_[1]->ptr;
-    tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), X, A, A + 2 * s_.P);
+    float* const hi[2] = {F32(kFh), F32(kD3)};
+    float* const lo[2] = {F32(kD2), F32(kEA)};
+    tf32_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), X, hi[0], lo[0]);
     FCGLE_LAUNCHED(launches);
-    const float* src = A;
+    int cur = 0;
     for (int mu = 0; mu < s_.d; ++mu) {
       const bool last = mu == s_.d - 1;
-      float* dst = last ? Y : (src == A ? B : A);
-      launch_tf32(src, src + 2 * s_.P, mu, fwd, dst, last ? nullptr : dst + 2 * s_.P);
-      src = dst;
+      launch_tf32(hi[cur], lo[cur], mu, fwd, last ? Y : hi[cur ^ 1], last ? nullptr : lo[cur ^ 1]);
+      cur ^= 1;
     }
   }
 
@@ -1458,7 +1457,6 @@ class EngineB3 : public EngineBase {
   std::unique_ptr<DevMem<__nv_bfloat16>> sp_[kNumSplit];
   std::unique_ptr<DevMem<float>> src_[kMaxSrc];
   std::unique_ptr<DevMem<float>> host_stage_;
-  std::unique_ptr<DevMem<float>> tsp_[2];   // split-TF32 work tensors of the precise transforms
   Direction dir_[kMaxDim];
   int exp_form_ = FCGLE_EXP_TUCKER;
   std::map<uint64_t, std::vector<std::unique_ptr<CMat>>> ecache_;
