@@ -92,3 +92,20 @@ def test_norm_static_wrapper_rejects_mismatched_tensors(binding, case):
         binding.fcgle_norm_static(p, u)
     assert e.value.status == binding.FCGLE_ERR_INVALID_ARG
     assert {"dtype": "dtype", "numel": "entries", "contiguous": "contiguous", "device": "CUDA"}[case] in str(e.value)
+
+
+def test_new_entry_points_reject_null_handles(binding):
+    lib = binding._lib
+    assert lib.fcgle_set_exp_form(None, 1) == binding.FCGLE_ERR_INVALID_ARG
+    s = (ctypes.c_double * 1)(1.0)
+    o = (ctypes.c_double * 2)()
+    assert lib.fcgle_spectral_scalars(None, 2, 1, 1e-3, 1, s, o, 0) == binding.FCGLE_ERR_INVALID_ARG
+    assert lib.fcgle_mode_product(None, 0, 1, None, None) == binding.FCGLE_ERR_INVALID_ARG
+
+
+def test_autotune_report_without_tuning(binding):
+    # nothing has been tuned in this process (no GPU here): the report is empty
+    need = ctypes.c_size_t()
+    assert binding._lib.fcgle_autotune_report(None, 0, ctypes.byref(need)) == binding.FCGLE_OK
+    assert need.value >= 1
+    assert isinstance(binding.fcgle_autotune_report(), str)
