@@ -127,6 +127,9 @@ typedef struct fcgle_ctx* fcgle_handle;
  * 1e-11 relative), copies Q_mu and lam_mu to the device once (Sec. 4.2: the
  * only host-to-device transfer of the method) and allocates the work
  * buffers.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * For BF16X3 handles the setup also runs the kernel autotuner (see
+ * fcgle_autotune_report) on that stream for problem shapes this process has
+ * not tuned yet, and waits for it; do not call it during a stream capture.
  * On success *out owns everything; release it with fcgle_destroy. */
 fcgle_status fcgle_setup(const fcgle_params* params, void* cuda_stream, fcgle_handle* out);
 
@@ -346,6 +349,9 @@ fcgle_status fcgle_destroy(fcgle_handle h);
  * sources present (time-dependent steps) it enqueues the kernels directly. */
 typedef struct fcgle_batch_ctx* fcgle_batch;
 
+/* Creates the instances (in parallel host threads), then synchronises the
+ * device and runs the autotuner for each instance in turn, so that no other
+ * work overlaps its timing launches. */
 fcgle_status fcgle_batch_create(int count, const fcgle_params* params, void* cuda_stream, int nstreams,
                                 fcgle_batch* out);
 
