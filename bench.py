@@ -34,6 +34,13 @@ ALPHAS = [1.2, 1.5, 1.8]
 PARS = dict(nu=1.0, eta=0.5, gamma=1.0, kappa=1.0, zeta=0.5)
 TAU = 1e-3
 KROGSTAD_BYTES_PER_ELEM = 16 * 16 + 32 + 3 * 24 + 32 + 40 + 40 + 24   # 496 B per complex element
+SLAB_SAVED_BYTES_PER_ELEM = 8 * 16   # slab-fused modes 1 + 2: one 16-byte pass less per Tucker operator
+
+
+def tucker_form_of(report, n):
+    """'slab-fused' or 'rotating': the autotuner's choice for an n^3 handle."""
+    m = re.search(r"tucker p=\(%d,%d,%d\):.*-> (\S+)" % (n, n, n), report)
+    return m.group(1) if m else "rotating"
 
 # 2D 1023 x 1024 workload (linearly-implicit Euler and ETD2RK, 500 steps): the
 # mode products contract p = 1024, so they are bound by the tensor pipe, not HBM
@@ -266,6 +273,31 @@ def l2_flush_buffer(torch):
     return torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
 
+def tf32_peak_tflops(torch, n=8192, reps=5):
+    """TF32 tensor-core matrix-multiply rate, measured here: torch.matmul on
+    n x n float32 operands with TF32 allowed (cuBLAS), best of reps, CUDA events."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, dtype=torch.float32, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float32, device="cuda")
+        c = a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
 def dgemm_peak_tflops(torch, n=4096, reps=5):
     """FP64 matrix-multiply rate of this GPU, measured here: torch.matmul on
     n x n float64 operands (cuBLAS DGEMM), best of reps, CUDA events."""
@@ -286,21 +318,26 @@ def dgemm_peak_tflops(torch, n=4096, reps=5):
     return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
-def kernel_source_sha():
-    """sha256[:16] of the plain mode-product kernel's sources (b3_plain.cuh, then b3_kernel.cuh)."""
+PLAIN_SOURCES = ("b3_plain.cuh", "b3_kernel.cuh")
+SLAB_SOURCES = ("b3_slab.cuh", "b3_kernel.cuh")
+
+
+def kernel_source_sha(files=PLAIN_SOURCES):
+    """sha256[:16] of a kernel's sources (the files in order; the plain mode
+    product: b3_plain.cuh, then b3_kernel.cuh)."""
     h = hashlib.sha256()
-    for f in ("b3_plain.cuh", "b3_kernel.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2510_21394_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n):
-    """DRAM bytes per launch of the mode-product kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    prof = os.path.join(ROOT, "profiles", "mp_b3_plain_256cube.md")
+def ncu_traffic(n, profile="mp_b3_plain_256cube.md", files=PLAIN_SOURCES):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if the
+    summary was taken on the current kernel source."""
+    prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(files)
     text = open(prof).read()
     m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic bytes per launch \(scaled to %d\^3\):\s*([0-9.eE+]+)" % n, text)
@@ -432,17 +469,67 @@ def run_ours(args, rank, world, local_rank):
     mp_bytes = 2 * (2 * P * 4)       # read X, write Y (hi + lo bf16 = 4 B per real)
     peak, peak_kind = measured_peaks()
     achieved = mp_bytes / (mp_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(n),
-                "kernel": "mp_b3_plain_kernel (one 256^3 mode product, split in/out)", "peak_kind": f"{peak_kind} hbm_gbs (burst)",
-                "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
+    plain_roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                  "frac": round(achieved / peak, 4), "traffic": ncu_traffic(n),
+                  "kernel": "mp_b3_plain_kernel (one 256^3 mode product, split in/out)",
+                  "peak_kind": f"{peak_kind} hbm_gbs (burst)", "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
+    # ---- the slab-fused mode-1 + mode-2 product and the natural-order mode-3 product
+    form = tucker_form_of(fcgle.fcgle_autotune_report(), n)
+    timed = {}
+    for name, d_, fl in (("slab12", 0, 1 | 2 | 8), ("mn3", 2, 1 | 2 | 16)):
+        fcgle.fcgle_mode_product(solver.h, d_, fl, X, Y)
+        torch.cuda.synchronize()
+        k0.record(stream)
+        for _ in range(reps):
+            fcgle.fcgle_mode_product(solver.h, d_, fl, X, Y)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        solver.sync()
+        timed[name] = k0.elapsed_time(k1) / reps
+    # FLOPs of the slab kernel: two mode products, 3 split passes, 2 p flops per real element
+    sl_flops = 2 * 3 * 2 * n * 2 * P
+    bf_peak, _, bf_kind = measured_bf16_peak()
+    sl_tf = sl_flops / (timed["slab12"] / 1e3) / 1e12
+    slab_roof = {"bound": "tensor", "achieved": round(sl_tf, 1), "peak": bf_peak, "unit": "TFLOP/s",
+                 "frac": round(sl_tf / bf_peak, 4),
+                 "traffic": ncu_traffic(n, "mp_b3_slab12_256cube.md", SLAB_SOURCES),
+                 "kernel": "mp_b3_slab12_kernel (modes 1 + 2 of a 256^3 Tucker operator, split in/out)",
+                 "peak_kind": f"{bf_kind} bf16_tflops (burst)", "launch_ms": round(timed["slab12"], 4),
+                 "algorithmic_flops": sl_flops, "algorithmic_bytes": mp_bytes,
+                 "hbm_frac": round(mp_bytes / (timed["slab12"] / 1e3) / 1e9 / peak, 4)}
+    mn_gbs = mp_bytes / (timed["mn3"] / 1e3) / 1e9
+    mn_roof = {"bound": "hbm", "achieved": round(mn_gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(mn_gbs / peak, 4),
+               "kernel": "mp_b3_kernel<EpiStoreSplitGen, natural order> (mode 3 on the slab kernel's output)",
+               "launch_ms": round(timed["mn3"], 4), "algorithmic_bytes": mp_bytes}
+    roofline = slab_roof if form == "slab-fused" else plain_roof
     del X, Y
+    # ---- the precise end-transform product (split-TF32 on the tensor cores, FP32 in and out:
+    # the split pass 24 B + the product 24 B per complex element), per launch pair
+    Xf = torch.randn(2 * P, device="cuda", dtype=torch.float32)
+    Yf = torch.empty_like(Xf)
+    fcgle.fcgle_mode_product(solver.h, 0, 1 | 4, Xf, Yf)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        fcgle.fcgle_mode_product(solver.h, 0, 1 | 4, Xf, Yf)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    solver.sync()
+    pt_ms = k0.elapsed_time(k1) / reps
+    pt_bytes = 48 * P
+    precise = {"kernels": "tf32_split_kernel + mp_b3_plain_kernel<kOpTF32F> (one 256^3 product, FP32 in/out)",
+               "ms": round(pt_ms, 4), "achieved_gbs": round(pt_bytes / (pt_ms / 1e3) / 1e9, 1),
+               "frac_of_hbm": round(pt_bytes / (pt_ms / 1e3) / 1e9 / peak, 4), "algorithmic_bytes": pt_bytes,
+               "tflops": round(3 * 2 * n * 2 * P / (pt_ms / 1e3) / 1e12, 1)}
+    del Xf, Yf
     # the whole step against HBM: algorithmic bytes per element of one Krogstad step
     # (16 plain products x 16 B; EpiFhat 32, 3 x EpiStageD 24, EpiKrog2 32, EpiKrog3 40,
     # EpiKrogFinal 40, EpiUpdateG 24) over the padded tensor
     step_roof = None
     if args.scheme == "krogstad":
-        step_bytes = KROGSTAD_BYTES_PER_ELEM * P
+        step_bytes = (KROGSTAD_BYTES_PER_ELEM - (SLAB_SAVED_BYTES_PER_ELEM if form == "slab-fused" else 0)) * P
         step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
         step_roof = {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(step_gbs / peak, 4), "floor_ms": round(step_bytes / (peak * 1e9) * 1e3, 4)}
@@ -499,6 +586,9 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         extra["autotune"] = fcgle.fcgle_autotune_report().strip().splitlines()
+        extra["precise_transform"] = precise
+        extra["tucker_form"] = form
+        extra["kernels"] = {"plain": plain_roof, "slab12": slab_roof, "mn3": mn_roof}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "config": workload_config(n, "bf16x3", args.scheme, args.tau, args.exp_form),
@@ -657,6 +747,9 @@ def run_config2(args, rank, world, local_rank):
         s64.sync()
         s64.close()
         del X64, Y64
+        extra["tf32_peak_tflops"] = {"value": round(tf32_peak_tflops(torch), 1),
+                                     "how": "measured here: cuBLAS TF32 (torch.matmul float32, TF32 allowed, 8192^3, "
+                                            "best of 5); context for the split-TF32 end transforms"}
         extra["fp64_gpu"] = f64
         extra["fp64_roofline"] = {"bound": "fp64", "achieved": round(tf64, 3), "peak": round(dpeak, 3),
                                   "unit": "TFLOP/s", "frac": round(tf64 / dpeak, 4),

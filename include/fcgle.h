@@ -170,6 +170,24 @@ fcgle_status fcgle_set_coefficients(fcgle_handle h, double nu, double eta, doubl
 typedef enum { FCGLE_EXP_TUCKER = 0, FCGLE_EXP_KRON = 1 } fcgle_exp_form;
 fcgle_status fcgle_set_exp_form(fcgle_handle h, int form);
 
+/* How a Tucker operator X x_1 M_1 x_2 M_2 x_3 M_3 (Eq. fKu_diag, Sec. 3.2)
+ * of a 3D BF16X3 handle is run.  FCGLE_TUCKER_ROTATING: three mode products,
+ * each reading the tensor with its contracted index fastest and writing the
+ * new index slowest (16 bytes of HBM traffic per element and product).
+ * FCGLE_TUCKER_SLAB: the mode-1 and mode-2 products fused per j_3 slab (the
+ * intermediate stays in tensor memory; 16 bytes per element for the two),
+ * then the mode-3 product reading the natural order with j_3 slowest; needs
+ * p_2 <= 256, else FCGLE_ERR_UNSUPPORTED.  FCGLE_TUCKER_AUTO (the default):
+ * the form the autotuner found faster for the handle's extents (see
+ * fcgle_autotune_report).  The two forms round differently (both at the
+ * split-BF16 level); the first and last Tucker operators of a time
+ * integration (the precise split-TF32 transforms) and batches always use the
+ * rotating form.  Other handles (FP64, d != 3) accept FCGLE_TUCKER_AUTO and
+ * FCGLE_TUCKER_ROTATING and run their only form; FCGLE_TUCKER_SLAB gives
+ * FCGLE_ERR_UNSUPPORTED there.  Any other value: FCGLE_ERR_INVALID_ARG. */
+typedef enum { FCGLE_TUCKER_AUTO = 0, FCGLE_TUCKER_ROTATING = 1, FCGLE_TUCKER_SLAB = 2 } fcgle_tucker_form;
+fcgle_status fcgle_set_tucker_form(fcgle_handle h, int form);
+
 /* out = f(theta K) v with f = 1/(1-z) (func INV), e^z (EXP, Eq. Neudeckerd)
  * or phi_k (PHI, k in 0..4).  v and out are device tensors in the user layout
  * and may alias. */
@@ -312,9 +330,14 @@ fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P);
  * tensor-core products hi.hi + hi.lo + lo.hi, about 2^-21 relative) when
  * d >= 2, R is a multiple of 8 and p_mu <= 256 (the tensor core's FP32
  * accumulation error grows with the contracted length), FP32 on the CUDA
- * cores otherwise.  Other
- * flag bits give FCGLE_ERR_INVALID_ARG.  X and Y must not overlap.  direction
- * in 0..d-1. */
+ * cores otherwise.  flags bit 3 (BF16X3 handles, d = 3, p_2 <= 256, with
+ * bit 1, direction 0): the slab-fused mode-1 and mode-2 products in the
+ * natural order, Y[c][j3][i2][i1] = sum M_2[i2][j2] M_1[i1][j1]
+ * X[c][j3][j2][j1] with M_mu = Q_mu^T (bit 0) or Q_mu.  flags bit 4 (BF16X3
+ * handles, d >= 2, R % 8 == 0, with bit 1, direction d-1): the product above
+ * with X read in the natural order, X[c][k][r] (direction mu slowest); Y as
+ * above.  Other flag bits or combinations give FCGLE_ERR_INVALID_ARG.  X and
+ * Y must not overlap.  direction in 0..d-1. */
 fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y);
 
 /* The kernel autotuner (a library facility, not a step of the method).  The
@@ -325,7 +348,9 @@ fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const 
  * fcgle_setup and fcgle_batch_create time every eligible configuration once
  * per process for each new (p, R) a handle runs the plain product on, on the
  * handle's work buffers (synchronously, a few kernel launches each), and the
- * fastest is used from then on.  The environment variable FCGLE_PLAIN_CFG=<id>
+ * fastest is used from then on.  For 3D handles fcgle_setup also times one
+ * Tucker operator in the rotating and in the slab-fused form
+ * (fcgle_set_tucker_form) once per process per extents (p_1, p_2, p_3).  The environment variable FCGLE_PLAIN_CFG=<id>
  * (0..3, read once) forces one configuration where it is eligible.
  * This call writes a text report, one line per tuned shape with the time of
  * every eligible configuration and the choice, into buf (size bytes,

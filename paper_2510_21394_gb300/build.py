@@ -44,7 +44,8 @@ def _stale(target, deps):
 
 def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+               + glob.glob(os.path.join(ROOT, "include", "*.h")))
     srcs = _sources()
     objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in srcs]
     cc = nvcc()

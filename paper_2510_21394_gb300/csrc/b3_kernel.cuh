@@ -156,11 +156,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   // K-major, SWIZZLE_128B: rows of 128 bytes, 8-row groups 1024 bytes apart.
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// MN-major, SWIZZLE_128B: every k is a 128-byte row of 64 consecutive n, 8-row
+// (k) groups 1024 bytes apart (stride byte offset); the next 64 n start
+// `mn_stride` bytes further (leading byte offset).  Used with the instruction
+// descriptor's transpose-B bit.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t addr, uint32_t mn_stride) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+constexpr uint32_t kTransB = 1u << 16;   // instruction descriptor: B is MN-major
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
@@ -228,13 +244,21 @@ struct FusedDesc {
 // Grouped form (G = true): one persistent launch serves the last mode
 // product of several independent problems; maps, sizes and the epilogue
 // functor of problem k come from gd[k].  Same arithmetic per unit.
-template <class Epi, bool G = false, bool CX = false>
+//
+// Natural-order input (MN = true): X holds the contracted index as its
+// SLOWEST index, X[c][k][r], the layout the slab-fused mode-1+2 product
+// (b3_slab.cuh) leaves behind, so no rotation precedes this product.  The X
+// tensor maps are 3D (r, k, plane) with 64 x 64 boxes (64 r of one k per
+// 128-byte row), and the B operand is read MN-major; the accumulator, the
+// epilogue and the output layout Y[c][i][r] are those of the K-major form.
+template <class Epi, bool G = false, bool CX = false, bool MN = false>
 __global__ void __launch_bounds__(Cfg<Epi, CX>::kThreads, 1)
     mp_b3_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                  const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
                  const KParams kp, const Epi epi, const FusedDesc<Epi>* __restrict__ gd, int ngd,
                  long long gunits) {
   static_assert(!(G && CX), "the complex form has no grouped variant");
+  static_assert(!(MN && (G || CX)), "the natural-order form is single-problem and real");
   constexpr int NSTAGE = Cfg<Epi, CX>::kStages;
   constexpr int NEPI = Cfg<Epi, CX>::kEpi;
   constexpr uint32_t kStg = Cfg<Epi, CX>::kStageBytes;
@@ -326,10 +350,18 @@ __global__ void __launch_bounds__(Cfg<Epi, CX>::kThreads, 1)
             tma_load_2d(st + 32768, mmh, kc * BK, kp.ei_row + mb * BM, full_bar(s));
             tma_load_2d(st + 49152, mml, kc * BK, kp.ei_row + mb * BM, full_bar(s));
           }
-          tma_load_2d(st + kOffX, mxh, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + kOffX + 8192, mxh, kc * BK, r1, full_bar(s));
-          tma_load_2d(st + kOffX + 16384, mxl, kc * BK, r0, full_bar(s));
-          tma_load_2d(st + kOffX + 16384 + 8192, mxl, kc * BK, r1, full_bar(s));
+          if constexpr (MN) {
+            // 64 k-rows of 64 r, real plane then imaginary plane
+            tma_load_3d(st + kOffX, mxh, r0, kc * BK, 0, full_bar(s));
+            tma_load_3d(st + kOffX + 8192, mxh, r0, kc * BK, 1, full_bar(s));
+            tma_load_3d(st + kOffX + 16384, mxl, r0, kc * BK, 0, full_bar(s));
+            tma_load_3d(st + kOffX + 16384 + 8192, mxl, r0, kc * BK, 1, full_bar(s));
+          } else {
+            tma_load_2d(st + kOffX, mxh, kc * BK, r0, full_bar(s));
+            tma_load_2d(st + kOffX + 8192, mxh, kc * BK, r1, full_bar(s));
+            tma_load_2d(st + kOffX + 16384, mxl, kc * BK, r0, full_bar(s));
+            tma_load_2d(st + kOffX + 16384 + 8192, mxl, kc * BK, r1, full_bar(s));
+          }
         }
       }
       // drain: every issued stage must have landed before the CTA may exit
@@ -341,7 +373,7 @@ __global__ void __launch_bounds__(Cfg<Epi, CX>::kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                 ((uint32_t)(BM >> 4) << 24);
+                                 ((uint32_t)(BM >> 4) << 24) | (MN ? kTransB : 0u);
       constexpr uint32_t idesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BR >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
       uint32_t g = 0, t = 0;
@@ -368,6 +400,15 @@ __global__ void __launch_bounds__(Cfg<Epi, CX>::kThreads, 1)
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint32_t off = ks * 32;
             const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+            if constexpr (MN) {
+              // k-step ks = k-rows 16 ks .. 16 ks + 15 (2048 bytes in); the
+              // imaginary plane's 64 r follow 8 KB after the real plane's
+              const uint64_t bh = sw128_mn_desc(bhi + ks * 2048, 8192), bl = sw128_mn_desc(blo + ks * 2048, 8192);
+              mma_bf16(d_tmem, sw128_desc(ahi + off), bh, idesc, acc0);
+              mma_bf16(d_tmem, sw128_desc(ahi + off), bl, idesc, 1u);
+              mma_bf16(d_tmem, sw128_desc(alo + off), bh, idesc, 1u);
+              continue;
+            }
             mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
             mma_bf16(d_tmem, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
             mma_bf16(d_tmem, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);

@@ -208,6 +208,14 @@ fcgle_status fcgle_set_exp_form(fcgle_handle h, int form) {
   });
 }
 
+fcgle_status fcgle_set_tucker_form(fcgle_handle h, int form) {
+  return guarded([&] {
+    check_handle(h);
+    h->eng->set_tucker_form(form);
+    ++h->gen;
+  });
+}
+
 fcgle_status fcgle_apply_f(fcgle_handle h, int func, int k, double theta, const void* v, void* out) {
   return guarded([&] {
     check_handle(h);
@@ -355,7 +363,7 @@ fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const 
     check_handle(h);
     if (!X || !Y) throw InvalidArg("tensor pointer is NULL");
     if (X == Y) throw InvalidArg("X and Y must not overlap");
-    if (flags & ~7) throw InvalidArg("unknown flags");
+    if (flags & ~31) throw InvalidArg("unknown flags");
     h->eng->mode_product_flags(direction, flags, X, Y);
   });
 }

@@ -46,6 +46,12 @@ class EngineBase {
   virtual void set_exp_form(int form) {
     if (form != FCGLE_EXP_TUCKER && form != FCGLE_EXP_KRON) throw InvalidArg("unknown exponential form");
   }
+  // how a Tucker operator of a 3D split-BF16 handle is run (fcgle_tucker_form);
+  // other engines only validate the value
+  virtual void set_tucker_form(int form) {
+    if (form < FCGLE_TUCKER_AUTO || form > FCGLE_TUCKER_SLAB) throw InvalidArg("unknown Tucker-operator form");
+    if (form == FCGLE_TUCKER_SLAB) throw Unsupported("the slab-fused form is a 3D split-BF16 form");
+  }
   virtual void apply_f(int func, int k, double theta, const void* v, void* out) = 0;
   virtual void step(int scheme, double tau, double t, void* u) = 0;
   virtual void integrate(int scheme, double tau, int nsteps, double t0, const void* u0, void* uT) = 0;
@@ -56,9 +62,11 @@ class EngineBase {
                        int ckpt_every, void* grad_u0, double* grad_params, double* loss) = 0;
   virtual void mode_product(int mu, bool fwd, const void* X, void* Y) = 0;
   // flags: bit 0 forward (Q^T), bit 1 split-bf16 input and output, bit 2 the
-  // precise (split-TF32) product on FP32 input and output (bits 1, 2: BF16X3 only)
+  // precise (split-TF32) product on FP32 input and output, bit 3 the
+  // slab-fused modes 1 + 2, bit 4 the natural-order last product (bits 1-4:
+  // BF16X3 only)
   virtual void mode_product_flags(int mu, int flags, const void* X, void* Y) {
-    if (flags & 6) throw InvalidArg("flags bits 1 and 2 need a BF16X3 handle");
+    if (flags & 30) throw InvalidArg("flags bits 1 to 4 need a BF16X3 handle");
     mode_product(mu, flags & 1, X, Y);
   }
   virtual size_t internal_elems() const = 0;

@@ -33,6 +33,7 @@
 #include "b3_epilogues.cuh"
 #include "b3_kernel.cuh"
 #include "b3_plain.cuh"
+#include "b3_slab.cuh"
 #include "engine.h"
 
 namespace fcgle {
@@ -120,6 +121,15 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, long long>, TuneEntry> g_tune;   // (p, R)
 
+// Tucker-operator form of 3D handles (p1, p2, p3): the rotating chain of
+// three products, or the slab-fused modes 1 + 2 followed by the natural-order
+// mode-3 product; timed once per process per shape at setup.
+struct SlabTune {
+  float us_rot = -1.f, us_slab = -1.f;
+  bool slab = false;
+};
+std::map<std::tuple<int, int, int>, SlabTune> g_slab;
+
 bool tuned_lookup(int p, long long R, TuneEntry& e) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(std::make_tuple(p, R));
@@ -152,6 +162,12 @@ std::string plain_tune_report() {
         out.append(line, (size_t)n);
       }
     n = std::snprintf(line, sizeof(line), " -> %s\n", kPlainCfgName[kv.second.cfg]);
+    out.append(line, (size_t)n);
+  }
+  for (const auto& kv : g_slab) {
+    const int n = std::snprintf(line, sizeof(line), "tucker p=(%d,%d,%d): rotating %.2fus slab-fused %.2fus -> %s\n",
+                                std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                                kv.second.us_rot, kv.second.us_slab, kv.second.slab ? "slab-fused" : "rotating");
     out.append(line, (size_t)n);
   }
   return out;
@@ -204,6 +220,20 @@ void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p)
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
+}
+
+// 3D bf16 tensor map (dims d0 fastest), the given box and swizzle.
+void encode_bf16_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+                    bool swizzle) {
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  cuuint32_t box[3] = {b0, b1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           swizzle ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (3D) failed (" + std::to_string((int)r) + ")");
 }
 
 // 2D FP32 tensor map, SWIZZLE_128B, box (32 inner = 128 bytes, box_rows outer):
@@ -445,6 +475,24 @@ class EngineB3 : public EngineBase {
       set_smem_attr<b3::EpiLRK2A>();
       set_smem_attr<b3::EpiLRK2B>();
       set_smem_attr<b3::EpiStrangB>();
+      set_smem_attr_mn<b3::EpiStoreSplitGen>();
+      set_smem_attr_mn<b3::EpiStoreF32>();
+      set_smem_attr_mn<b3::EpiScaleF>();
+      set_smem_attr_mn<b3::EpiUpdateG>();
+      set_smem_attr_mn<b3::EpiStageD>();
+      set_smem_attr_mn<b3::EpiFhat>();
+      set_smem_attr_mn<b3::EpiKrog2>();
+      set_smem_attr_mn<b3::EpiKrog3>();
+      set_smem_attr_mn<b3::EpiKrogFinal>();
+      set_smem_attr_mn<b3::EpiEtd2>();
+      set_smem_attr_mn<b3::EpiSpecStep>();
+      set_smem_attr_mn<b3::EpiLBDF2S>();
+      set_smem_attr_mn<b3::EpiExtrapG>();
+      set_smem_attr_mn<b3::EpiLRK2A>();
+      set_smem_attr_mn<b3::EpiLRK2B>();
+      set_smem_attr_mn<b3::EpiStrangB>();
+      FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_slab12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)b3::kSlSmemBytes));
       set_smem_attr_cx<b3::EpiStoreF32>();
       set_smem_attr_cx<b3::EpiStoreSplitGen>();
       set_smem_attr_cx<b3::EpiUpdateG>();
@@ -511,6 +559,13 @@ class EngineB3 : public EngineBase {
     exp_form_ = form;
   }
 
+  void set_tucker_form(int form) override {
+    if (form < FCGLE_TUCKER_AUTO || form > FCGLE_TUCKER_SLAB) throw InvalidArg("unknown Tucker-operator form");
+    if (form == FCGLE_TUCKER_SLAB && !slab_ok())
+      throw Unsupported("the slab-fused form needs d == 3 and p_2 <= 256");
+    tucker_form_ = form;
+  }
+
   void spectral_scalars(int func, int k, double theta, int count, const double* s_host, double* out_host,
                         int flags) override {
     const bool ray = flags & 1;
@@ -550,6 +605,24 @@ class EngineB3 : public EngineBase {
         launch_tf32(ah, al, mu, fwd, (float*)Y, nullptr);
       } else {
         mp_f32((const float*)X, (float*)Y, mat_[mu][fwd ? 0 : 1].f32, s_.p[mu], (size_t)R, st_, launches);
+      }
+      return;
+    }
+    if (flags & 24) {
+      // natural-order forms (split input and output)
+      if (!(flags & 2)) throw InvalidArg("flags bits 3 and 4 need the split form (bit 1)");
+      if ((flags & 24) == 24) throw InvalidArg("flags bits 3 and 4 exclude each other");
+      const __nv_bfloat16* xh = (const __nv_bfloat16*)X;
+      __nv_bfloat16* yh = (__nv_bfloat16*)Y;
+      SplitOut in{const_cast<__nv_bfloat16*>(xh), const_cast<__nv_bfloat16*>(xh) + 2 * s_.P};
+      SplitOut out{yh, yh + 2 * s_.P};
+      if (flags & 8) {
+        if (!slab_ok() || mu != 0) throw InvalidArg("the slab-fused product needs d == 3, p_2 <= 256, direction 0");
+        launch_slab12(in, out, fwd);
+      } else {
+        if (s_.d < 2 || mu != s_.d - 1 || (P_ / s_.p[mu]) % 8 != 0)
+          throw InvalidArg("the natural-order product needs d >= 2, direction d - 1 and R % 8 == 0");
+        launch_mp_mn(in.hi, in.lo, fwd, b3::EpiStoreSplitGen{P32(), out});
       }
       return;
     }
@@ -699,6 +772,11 @@ class EngineB3 : public EngineBase {
   static void set_smem_attr() {
     FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)b3::Cfg<Epi>::kSmemBytes));
+  }
+  template <class Epi>
+  static void set_smem_attr_mn() {
+    FCGLE_CUDA(cudaFuncSetAttribute(b3::mp_b3_kernel<Epi, false, false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b3::Cfg<Epi>::kSmemBytes));
   }
   template <class Epi>
   static void set_smem_attr_cx() {
@@ -1044,6 +1122,55 @@ class EngineB3 : public EngineBase {
   // carries the fused epilogues) whose (p, R) the process has not tuned yet,
   // on the handle's work buffers, and records the fastest.  Synchronous.
   void autotune() override {
+    tune_plain();
+    tune_slab();
+  }
+
+  // 3D handles: times one forward Tucker operator (split output) in the
+  // rotating form and in the slab-fused form, once per process per shape,
+  // and keeps the slab-fused form where it is clearly faster.
+  void tune_slab() {
+    if (!slab_ok()) return;
+    const auto key = std::make_tuple(s_.p[0], s_.p[1], s_.p[2]);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      if (g_slab.count(key)) return;
+    }
+    SlabTune e;
+    const int keep = tucker_form_;
+    const b3::EpiStoreSplitGen ep{P32(), SP(kW)};
+    cudaEvent_t e0, e1;
+    FCGLE_CUDA(cudaEventCreate(&e0));
+    FCGLE_CUDA(cudaEventCreate(&e1));
+    try {
+      constexpr int kReps = 5;
+      for (int form : {FCGLE_TUCKER_ROTATING, FCGLE_TUCKER_SLAB}) {
+        tucker_form_ = form;
+        tucker(SP(kV), true, ep);   // warm-up
+        FCGLE_CUDA(cudaEventRecord(e0, st_));
+        for (int r = 0; r < kReps; ++r) tucker(SP(kV), true, ep);
+        FCGLE_CUDA(cudaEventRecord(e1, st_));
+        FCGLE_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FCGLE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        (form == FCGLE_TUCKER_SLAB ? e.us_slab : e.us_rot) = 1e3f * ms / kReps;
+      }
+    } catch (...) {
+      tucker_form_ = keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    tucker_form_ = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e.slab = e.us_slab < 0.98f * e.us_rot;
+    if (device_error()) throw DeviceTimeout("a bounded device-side wait gave up while tuning the Tucker operator");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_slab.emplace(key, e);
+  }
+
+  void tune_plain() {
     if (forced_plain_cfg() >= 0) return;
     for (int mu = 0; mu + 1 < s_.d; ++mu) {
       const long long R = P_ / s_.p[mu];
@@ -1178,12 +1305,80 @@ class EngineB3 : public EngineBase {
     FCGLE_LAUNCHED(launches);
   }
 
+  // ---- slab-fused modes 1 + 2 and the natural-order mode-3 product (d == 3)
+  bool slab_ok() const { return s_.d == 3 && s_.p[1] <= 256; }
+  bool use_slab() const {
+    if (!slab_ok() || rec_ || tucker_form_ == FCGLE_TUCKER_ROTATING) return false;
+    if (tucker_form_ == FCGLE_TUCKER_SLAB) return true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_slab.find(std::make_tuple(s_.p[0], s_.p[1], s_.p[2]));
+    return it != g_slab.end() && it->second.slab;
+  }
+
+  // Y[c][j3][i2][i1] = sum M2[i2][j2] M1[i1][j1] X[c][j3][j2][j1] (in, out split, natural order, distinct)
+  void launch_slab12(SplitOut in, SplitOut out, bool fwd) {
+    const int p1 = s_.p[0], p2 = s_.p[1], p3 = s_.p[2];
+    const Mat& m1 = mat_[0][fwd ? 0 : 1];
+    const Mat& m2 = mat_[1][fwd ? 0 : 1];
+    b3::SlabParams sp;
+    sp.p1 = p1;
+    sp.p2 = p2;
+    sp.p3 = p3;
+    sp.n2 = (p2 + 15) / 16 * 16;
+    sp.mb1 = m1.m_pad / b3::BM;
+    sp.kc1 = m1.k_pad / b3::BK;
+    sp.kc2 = (sp.n2 + b3::BK - 1) / b3::BK;
+    sp.err = err_->ptr;
+    CUtensorMap txh, txl, tyh, tyl;
+    encode_bf16_3d(&txh, in.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::BK, (uint32_t)sp.n2, true);
+    encode_bf16_3d(&txl, in.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::BK, (uint32_t)sp.n2, true);
+    encode_bf16_3d(&tyh, out.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, false);
+    encode_bf16_3d(&tyl, out.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, false);
+    const long long units = (long long)p3 * sp.mb1;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    launch_pdl(b3::mp_b3_slab12_kernel, grid, b3::SL_THREADS, b3::kSlSmemBytes, st_, txh, txl, m1.tm_hi, m1.tm_lo,
+               m2.tm_hi, m2.tm_lo, tyh, tyl, sp);
+    FCGLE_LAUNCHED(launches);
+  }
+
+  // the last mode product (direction d - 1) on a natural-order input X[c][k][r]
+  template <class Epi>
+  void launch_mp_mn(const __nv_bfloat16* xh, const __nv_bfloat16* xl, bool fwd, const Epi& epi) {
+    const int mu = s_.d - 1;
+    const Mat& m = mat_[mu][fwd ? 0 : 1];
+    const long long R = P_ / s_.p[mu];
+    CUtensorMap txh, txl;
+    encode_bf16_3d(&txh, xh, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, true);
+    encode_bf16_3d(&txl, xl, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, true);
+    b3::KParams kp;
+    kp.R = R;
+    kp.p = s_.p[mu];
+    kp.m_blocks = m.m_pad / b3::BM;
+    kp.k_chunks = m.k_pad / b3::BK;
+    kp.tiles = (R + b3::BR - 1) / b3::BR;
+    kp.err = err_->ptr;
+    const long long units = kp.tiles * kp.m_blocks;
+    const int grid = (int)std::min<long long>(units, num_sms());
+    launch_pdl(b3::mp_b3_kernel<Epi, false, false, true>, grid, b3::Cfg<Epi>::kThreads, b3::Cfg<Epi>::kSmemBytes, st_,
+               txh, txl, m.tm_hi, m.tm_lo, kp, epi, (const b3::FusedDesc<Epi>*)nullptr, 0, 0LL);
+    FCGLE_LAUNCHED(launches);
+  }
+
   // Tucker operator on the split tensor `in` (consumed); the last mode product
   // runs `epi`, which may write into `in` (d >= 2: `in` is only read by the
   // first mode product; d == 1: `in` is first copied aside).
   template <class Epi>
   void tucker(SplitOut in, bool fwd, const Epi& epi) {
     const int d = s_.d;
+    if (use_slab()) {
+      // modes 1 + 2 per j_3 slab, then the mode-3 product on the natural order
+      SplitOut t = SP(kT0);
+      launch_slab12(in, t, fwd);
+      last_mp_ = true;
+      launch_mp_mn(t.hi, t.lo, fwd, epi);
+      last_mp_ = false;
+      return;
+    }
     SplitOut src = in;
     if (d == 1) {
       SplitOut t = SP(kT1);
@@ -1459,6 +1654,7 @@ class EngineB3 : public EngineBase {
   std::unique_ptr<DevMem<float>> host_stage_;
   Direction dir_[kMaxDim];
   int exp_form_ = FCGLE_EXP_TUCKER;
+  int tucker_form_ = FCGLE_TUCKER_AUTO;
   std::map<uint64_t, std::vector<std::unique_ptr<CMat>>> ecache_;
   std::unique_ptr<DevMem<double>> scratch_;
   std::unique_ptr<DevMem<int>> err_;

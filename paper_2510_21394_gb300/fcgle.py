@@ -32,6 +32,11 @@ FCGLE_EXP_TUCKER = 0
 FCGLE_EXP_KRON = 1
 EXP_FORMS = {"tucker": FCGLE_EXP_TUCKER, "kron": FCGLE_EXP_KRON}
 
+FCGLE_TUCKER_AUTO = 0
+FCGLE_TUCKER_ROTATING = 1
+FCGLE_TUCKER_SLAB = 2
+TUCKER_FORMS = {"auto": FCGLE_TUCKER_AUTO, "rotating": FCGLE_TUCKER_ROTATING, "slab": FCGLE_TUCKER_SLAB}
+
 FCGLE_F_INV = 0
 FCGLE_F_EXP = 1
 FCGLE_F_PHI = 2
@@ -47,7 +52,7 @@ EXPORTS = ["fcgle_setup", "fcgle_set_stream", "fcgle_set_source", "fcgle_apply_f
            "fcgle_internal_elems", "fcgle_mode_product", "fcgle_adjoint", "fcgle_set_coefficients",
            "fcgle_batch_create", "fcgle_batch_instance", "fcgle_batch_integrate", "fcgle_batch_launch_count",
            "fcgle_batch_destroy", "fcgle_norm_static", "fcgle_selftest_bounded_wait", "fcgle_spectral_scalars",
-           "fcgle_autotune_report", "fcgle_set_exp_form"]
+           "fcgle_autotune_report", "fcgle_set_exp_form", "fcgle_set_tucker_form"]
 
 
 class fcgle_params(ctypes.Structure):
@@ -99,6 +104,7 @@ def _load():
         "fcgle_spectral_scalars": [H, I, I, D, I, ctypes.POINTER(D), ctypes.POINTER(D), I],
         "fcgle_autotune_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
         "fcgle_set_exp_form": [H, I],
+        "fcgle_set_tucker_form": [H, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -214,6 +220,11 @@ def fcgle_set_coefficients(h, nu, eta, gamma, kappa, zeta):
 def fcgle_set_exp_form(h, form):
     form = EXP_FORMS[form] if isinstance(form, str) else int(form)
     _check(_lib.fcgle_set_exp_form(h, form))
+
+
+def fcgle_set_tucker_form(h, form):
+    form = TUCKER_FORMS[form] if isinstance(form, str) else int(form)
+    _check(_lib.fcgle_set_tucker_form(h, form))
 
 
 def fcgle_apply_f(h, func, k, theta, v, out):
@@ -397,6 +408,10 @@ class Solver:
     def set_exp_form(self, form):
         """'tucker' (default for bf16x3) or 'kron' (Kronecker-product form of e^{tau K})."""
         fcgle_set_exp_form(self.h, form)
+
+    def set_tucker_form(self, form):
+        """'auto' (default), 'rotating' or 'slab' (3D split-BF16: modes 1 + 2 fused per slab)."""
+        fcgle_set_tucker_form(self.h, form)
 
     def apply_f(self, func, k, theta, v, out=None):
         v = self._check_tensor(v.contiguous())
