@@ -28,9 +28,11 @@
 // and stage 2 starts on each 64-column k-chunk of U as soon as it is written.
 //
 // Warp roles (one CTA per SM, persistent over the units):
-//   warp 0      TMA producer: stage-1 chunks (M1 hi, lo 128 x 64; X hi, lo
-//               N2 x 64) and stage-2 chunks (M2 hi, lo N2 x 64) through a
-//               2-deep ring of 96 KB stages
+//   warp 0      TMA producer: stage-1 chunks (M1 hi, lo 128 x 32; X hi, lo
+//               N2 x 32) and stage-2 chunks (M2 hi, lo N2 x 32) through a
+//               4-deep ring of 48 KB stages (32-wide k-chunks: 64-byte rows,
+//               64-byte swizzle, so that more operand bytes are in flight
+//               per byte the MMA holds)
 //   warp 1      TMEM allocator (512 columns) and single-thread MMA issuer
 //   warps 2-9   convert and store; warp w owns TMEM lane quarter w % 4 and
 //               the 16-column groups (convert) or 32-column boxes (store) of
@@ -49,8 +51,9 @@ namespace b3 {
 
 constexpr int SL_NEPI = 8;
 constexpr int SL_THREADS = 32 * (2 + SL_NEPI);
-constexpr int SL_NS = 2;                       // ring stages
-constexpr uint32_t kSlStage = 98304;           // M1 hi 16K | M1 lo 16K | X hi 32K | X lo 32K  (stage 2: M2 hi 32K | M2 lo 32K)
+constexpr int SL_NS = 4;                       // ring stages
+constexpr int SL_K = 32;                       // k per chunk (one 64-byte bf16 row)
+constexpr uint32_t kSlStage = 49152;           // M1 hi 8K | M1 lo 8K | X hi 16K | X lo 16K  (stage 2: M2 hi 16K | M2 lo 16K)
 constexpr uint32_t kSlOffEpi = SL_NS * kSlStage;
 constexpr uint32_t kSlEpiWarp = 4096;          // one 32 x 32 bf16 box, hi and lo
 constexpr uint32_t kSlOffBar = kSlOffEpi + SL_NEPI * kSlEpiWarp;
@@ -62,8 +65,8 @@ struct SlabParams {
   int p1, p2, p3;   // padded extents
   int n2;           // N of both products: p2 rounded up to a multiple of 16 (<= 256)
   int mb1;          // 128-row blocks of i1
-  int kc1;          // 64-wide k-chunks of j1
-  int kc2;          // 64-wide k-chunks of j2 (ceil(n2 / 64))
+  int kc1;          // 32-wide k-chunks of j1
+  int kc2;          // 32-wide k-chunks of j2 (ceil(n2 / 32))
   int* err;
 };
 
@@ -82,6 +85,11 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
                : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// K-major, SWIZZLE_64B: rows of 64 bytes, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
 
 __global__ void __launch_bounds__(SL_THREADS, 1)
     mp_b3_slab12_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
@@ -102,11 +110,11 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   const uint32_t d2_full = smem_u32(&bars[2 * SL_NS + 1]);
   const uint32_t d_empty = smem_u32(&bars[2 * SL_NS + 2]);
   const uint32_t fin_bar = smem_u32(&bars[2 * SL_NS + 3]);
-  // U ready, per 64-column k-chunk of stage 2 (at most 4)
+  // U ready, per 64 columns (at most 4)
   auto u_full = [&](int c) { return smem_u32(&bars[2 * SL_NS + 4 + c]); };
-  static_assert((2 * SL_NS + 8) * 8 <= 128, "barrier area");
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSlOffBar + 128);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSlOffBar + 136);
+  static_assert((2 * SL_NS + 8) * 8 <= 192, "barrier area");
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSlOffBar + 192);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSlOffBar + 200);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < SL_NS; ++s) {
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
-      const uint32_t xbytes = (uint32_t)sp.n2 * 128;   // one N2 x 64 bf16 box
+      const uint32_t xbytes = (uint32_t)sp.n2 * 64;   // one N2 x 32 bf16 box
       const int m2boxes = sp.n2 > 128 ? 2 : 1;
       for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const int j3 = (int)(u / sp.mb1), b1 = (int)(u % sp.mb1);
@@ -150,20 +158,20 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
             const int s = (int)(g % SL_NS);
             if (!mbar_wait(empty_bar(s), ((g / SL_NS) & 1) ^ 1, abort_flag, err, 31)) { ok = false; break; }
             const uint32_t st = sbase + s * kSlStage;
-            mbar_arrive_tx(full_bar(s), 32768 + 2 * xbytes);
-            tma_load_2d(st, &tm_m1hi, kc * BK, b1 * BM, full_bar(s));
-            tma_load_2d(st + 16384, &tm_m1lo, kc * BK, b1 * BM, full_bar(s));
-            tma_load_3d(st + 32768, &tm_xhi, kc * BK, 0, z, full_bar(s));
-            tma_load_3d(st + 65536, &tm_xlo, kc * BK, 0, z, full_bar(s));
+            mbar_arrive_tx(full_bar(s), 16384 + 2 * xbytes);
+            tma_load_2d(st, &tm_m1hi, kc * SL_K, b1 * BM, full_bar(s));
+            tma_load_2d(st + 8192, &tm_m1lo, kc * SL_K, b1 * BM, full_bar(s));
+            tma_load_3d(st + 16384, &tm_xhi, kc * SL_K, 0, z, full_bar(s));
+            tma_load_3d(st + 32768, &tm_xlo, kc * SL_K, 0, z, full_bar(s));
           }
           for (int kc = 0; kc < sp.kc2 && ok; ++kc, ++g) {
             const int s = (int)(g % SL_NS);
             if (!mbar_wait(empty_bar(s), ((g / SL_NS) & 1) ^ 1, abort_flag, err, 32)) { ok = false; break; }
             const uint32_t st = sbase + s * kSlStage;
-            mbar_arrive_tx(full_bar(s), (uint32_t)m2boxes * 32768);
+            mbar_arrive_tx(full_bar(s), (uint32_t)m2boxes * 16384);
             for (int b = 0; b < m2boxes; ++b) {
-              tma_load_2d(st + b * 16384, &tm_m2hi, kc * BK, b * BM, full_bar(s));
-              tma_load_2d(st + 32768 + b * 16384, &tm_m2lo, kc * BK, b * BM, full_bar(s));
+              tma_load_2d(st + b * 8192, &tm_m2hi, kc * SL_K, b * BM, full_bar(s));
+              tma_load_2d(st + 16384 + b * 8192, &tm_m2lo, kc * SL_K, b * BM, full_bar(s));
             }
           }
         }
@@ -192,15 +200,15 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
             const int s = (int)(g % SL_NS);
             if (!mbar_wait(full_bar(s), (g / SL_NS) & 1, abort_flag, err, 34)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t ahi = sbase + s * kSlStage, alo = ahi + 16384;
-            const uint32_t bhi = ahi + 32768, blo = ahi + 65536;
+            const uint32_t ahi = sbase + s * kSlStage, alo = ahi + 8192;
+            const uint32_t bhi = ahi + 16384, blo = ahi + 32768;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
+            for (int ks = 0; ks < 2; ++ks) {
               const uint32_t off = ks * 32;
               const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-              mma_bf16(tmem_base, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, acc0);
-              mma_bf16(tmem_base, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, 1u);
-              mma_bf16(tmem_base, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+              mma_bf16(tmem_base, sw64_desc(ahi + off), sw64_desc(bhi + off), idesc, acc0);
+              mma_bf16(tmem_base, sw64_desc(ahi + off), sw64_desc(blo + off), idesc, 1u);
+              mma_bf16(tmem_base, sw64_desc(alo + off), sw64_desc(bhi + off), idesc, 1u);
             }
             mma_commit(empty_bar(s));
           }
@@ -212,19 +220,19 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
           if (!mbar_wait(d_empty, (t & 1) ^ 1, abort_flag, err, 41)) { ok = false; break; }
           for (int kc = 0; kc < sp.kc2; ++kc, ++g) {
             const int s = (int)(g % SL_NS);
-            if (!mbar_wait(u_full(kc), t & 1, abort_flag, err, 35)) { ok = false; break; }
+            if (!mbar_wait(u_full(kc >> 1), t & 1, abort_flag, err, 35)) { ok = false; break; }
             if (!mbar_wait(full_bar(s), (g / SL_NS) & 1, abort_flag, err, 36)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t bhi = sbase + s * kSlStage, blo = bhi + 32768;
+            const uint32_t bhi = sbase + s * kSlStage, blo = bhi + 16384;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const int kk = 4 * kc + ks;   // 16-wide k-step of j2
+            for (int ks = 0; ks < 2; ++ks) {
+              const int kk = 2 * kc + ks;   // 16-wide k-step of j2
               if (kk < ksteps2) {
                 const uint32_t uhi = tmem_base + 16 * kk, ulo = uhi + 8;
                 const uint32_t off = ks * 32, e_tmem = tmem_base + kSlColE;
-                mma_bf16_ts(e_tmem, uhi, sw128_desc(bhi + off), idesc, kk > 0 ? 1u : 0u);
-                mma_bf16_ts(e_tmem, uhi, sw128_desc(blo + off), idesc, 1u);
-                mma_bf16_ts(e_tmem, ulo, sw128_desc(bhi + off), idesc, 1u);
+                mma_bf16_ts(e_tmem, uhi, sw64_desc(bhi + off), idesc, kk > 0 ? 1u : 0u);
+                mma_bf16_ts(e_tmem, uhi, sw64_desc(blo + off), idesc, 1u);
+                mma_bf16_ts(e_tmem, ulo, sw64_desc(bhi + off), idesc, 1u);
               }
             }
             mma_commit(empty_bar(s));
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         // 64-column k-chunk (4 groups of 16, 2 per warp of a lane quarter) at a time
         if (!mbar_wait(d1_full, t & 1, abort_flag, err, 39)) { ok = false; break; }
         tc_fence_after();
-        for (int kc = 0; kc < sp.kc2; ++kc) {
+        for (int kc = 0; kc < (sp.n2 + 63) / 64; ++kc) {
           uint32_t v[2][16];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {

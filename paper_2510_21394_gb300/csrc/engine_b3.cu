@@ -222,15 +222,31 @@ void encode_bf16_out(CUtensorMap* map, const void* base, uint64_t R, uint64_t p)
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
 }
 
-// 3D bf16 tensor map (dims d0 fastest), the given box and swizzle.
+// 2D bf16 tensor map, SWIZZLE_64B, box (32 inner = 64 bytes, box_rows outer):
+// the operands of the slab-fused product, in 32-wide k-chunks.
+void encode_bf16_sw64(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (sw64) failed (" + std::to_string((int)r) + ")");
+}
+
+// 3D bf16 tensor map (dims d0 fastest), the given box and swizzle (0, 64 or 128 bytes).
 void encode_bf16_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
-                    bool swizzle) {
+                    int swizzle) {
   cuuint64_t dims[3] = {d0, d1, d2};
   cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
   cuuint32_t box[3] = {b0, b1, 1};
   cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = swizzle == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                : CU_TENSOR_MAP_SWIZZLE_NONE;
   CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                            swizzle ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled (3D) failed (" + std::to_string((int)r) + ")");
@@ -762,6 +778,7 @@ class EngineB3 : public EngineBase {
     float* tlo = nullptr;
     int p = 0, m_pad = 0, k_pad = 0, k_pad32 = 0;
     CUtensorMap tm_hi, tm_lo, tm_thi, tm_tlo;
+    CUtensorMap tm_hi64, tm_lo64;   // the same hi / lo in 32-wide, 64-byte-swizzled boxes (slab-fused product)
   };
 
   float* F32(int i) { return f32_[i]->ptr; }
@@ -947,6 +964,8 @@ class EngineB3 : public EngineBase {
     FCGLE_CUDA(cudaMemcpy(m.lo, lo.data(), bytes, cudaMemcpyHostToDevice));
     encode_bf16(&m.tm_hi, m.hi, m.k_pad, m.m_pad, b3::BM);
     encode_bf16(&m.tm_lo, m.lo, m.k_pad, m.m_pad, b3::BM);
+    encode_bf16_sw64(&m.tm_hi64, m.hi, m.k_pad, m.m_pad, b3::BM);
+    encode_bf16_sw64(&m.tm_lo64, m.lo, m.k_pad, m.m_pad, b3::BM);
     std::vector<float> f((size_t)p * p);
     for (size_t e = 0; e < f.size(); ++e) f[e] = (float)M[e];
     FCGLE_CUDA(cudaMalloc(&m.f32, f.size() * 4));
@@ -1326,18 +1345,18 @@ class EngineB3 : public EngineBase {
     sp.p3 = p3;
     sp.n2 = (p2 + 15) / 16 * 16;
     sp.mb1 = m1.m_pad / b3::BM;
-    sp.kc1 = m1.k_pad / b3::BK;
-    sp.kc2 = (sp.n2 + b3::BK - 1) / b3::BK;
+    sp.kc1 = (p1 + b3::SL_K - 1) / b3::SL_K;
+    sp.kc2 = (sp.n2 + b3::SL_K - 1) / b3::SL_K;
     sp.err = err_->ptr;
     CUtensorMap txh, txl, tyh, tyl;
-    encode_bf16_3d(&txh, in.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::BK, (uint32_t)sp.n2, true);
-    encode_bf16_3d(&txl, in.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::BK, (uint32_t)sp.n2, true);
-    encode_bf16_3d(&tyh, out.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, false);
-    encode_bf16_3d(&tyl, out.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, false);
+    encode_bf16_3d(&txh, in.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::SL_K, (uint32_t)sp.n2, 64);
+    encode_bf16_3d(&txl, in.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, b3::SL_K, (uint32_t)sp.n2, 64);
+    encode_bf16_3d(&tyh, out.hi, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, 0);
+    encode_bf16_3d(&tyl, out.lo, (uint64_t)p1, (uint64_t)p2, 2 * (uint64_t)p3, 32, 32, 0);
     const long long units = (long long)p3 * sp.mb1;
     const int grid = (int)std::min<long long>(units, num_sms());
-    launch_pdl(b3::mp_b3_slab12_kernel, grid, b3::SL_THREADS, b3::kSlSmemBytes, st_, txh, txl, m1.tm_hi, m1.tm_lo,
-               m2.tm_hi, m2.tm_lo, tyh, tyl, sp);
+    launch_pdl(b3::mp_b3_slab12_kernel, grid, b3::SL_THREADS, b3::kSlSmemBytes, st_, txh, txl, m1.tm_hi64,
+               m1.tm_lo64, m2.tm_hi64, m2.tm_lo64, tyh, tyl, sp);
     FCGLE_LAUNCHED(launches);
   }
 
@@ -1348,8 +1367,8 @@ class EngineB3 : public EngineBase {
     const Mat& m = mat_[mu][fwd ? 0 : 1];
     const long long R = P_ / s_.p[mu];
     CUtensorMap txh, txl;
-    encode_bf16_3d(&txh, xh, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, true);
-    encode_bf16_3d(&txl, xl, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, true);
+    encode_bf16_3d(&txh, xh, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, 128);
+    encode_bf16_3d(&txl, xl, (uint64_t)R, (uint64_t)s_.p[mu], 2, b3::BR, b3::BK, 128);
     b3::KParams kp;
     kp.R = R;
     kp.p = s_.p[mu];
