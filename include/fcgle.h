@@ -341,17 +341,18 @@ fcgle_status fcgle_internal_elems(fcgle_handle h, size_t* P);
 fcgle_status fcgle_mode_product(fcgle_handle h, int direction, int flags, const void* X, void* Y);
 
 /* The kernel autotuner (a library facility, not a step of the method).  The
- * split-BF16 plain mode product has several shared-memory ring
- * configurations (X ring 4 / 3 / 2 deep with the M ring taking the rest, or
- * the block of M resident in shared memory for p <= 256); the best one
- * depends on the contracted extent p and on the number of units per SM.
- * fcgle_setup and fcgle_batch_create time every eligible configuration once
- * per process for each new (p, R) a handle runs the plain product on, on the
- * handle's work buffers (synchronously, a few kernel launches each), and the
- * fastest is used from then on.  For 3D handles fcgle_setup also times one
- * Tucker operator in the rotating and in the slab-fused form
- * (fcgle_set_tucker_form) once per process per extents (p_1, p_2, p_3).  The environment variable FCGLE_PLAIN_CFG=<id>
- * (0..3, read once) forces one configuration where it is eligible.
+ * split-BF16 plain mode product has several tile and shared-memory ring
+ * configurations (X ring 4 / 3 / 2 deep with the M ring taking the rest, the
+ * block of M resident in shared memory for p <= 256, or wide tiles of 128 r
+ * per plane); the best one depends on the contracted extent p and on the
+ * number of units per SM.  fcgle_setup and fcgle_batch_create time every
+ * eligible configuration once per process for each new (p, R) a handle runs
+ * the plain product on, on the handle's work buffers (synchronously, a few
+ * kernel launches each), and the fastest is used from then on.  For 3D
+ * handles fcgle_setup also times one Tucker operator in the rotating and in
+ * the slab-fused form (fcgle_set_tucker_form) once per process per extents
+ * (p_1, p_2, p_3).  The environment variable FCGLE_PLAIN_CFG=<id> (0..5,
+ * read once) forces one configuration where it is eligible.
  * This call writes a text report, one line per tuned shape with the time of
  * every eligible configuration and the choice, into buf (size bytes,
  * NUL-terminated, truncated if short) and the full length + 1 into *needed

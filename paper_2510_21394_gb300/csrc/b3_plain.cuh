@@ -112,7 +112,13 @@ constexpr int kMaxRing = 4;       // barrier slots per ring
 //   CX:      the complex (Kronecker-product exponential) form: M = Er + i Ei,
 //            an M stage carries Er_hi, Er_lo, Ei_hi, Ei_lo (64 KB); X 2 + M 2
 //            (the products are those of the complex fused form, b3_kernel.cuh)
-template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false, bool CX = false, bool MH = false>
+//   W = 2:   wide tiles (single form, split-BF16): 128 r of each plane per
+//            unit, MMA N = 256, X stages of 64 KB (X 2 + M 2), two 256-column
+//            accumulators.  Every 32 KB chunk of M then feeds twice the MMA
+//            work, so a unit pulls 3/4 of the operand bytes per flop that a
+//            64-r unit does; the TMA ingest of an SM is what bounds the
+//            product at p = 256.
+template <bool G, int OP = kOpBF16, int NXR = PL_NX, bool MR = false, bool CX = false, bool MH = false, int W = 1>
 __global__ void __launch_bounds__(PL_THREADS, 1)
     mp_b3_plain_kernel(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                        const __grid_constant__ CUtensorMap tm_mhi, const __grid_constant__ CUtensorMap tm_mlo,
@@ -121,13 +127,17 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   static_assert(!(G && (MR || CX || MH)), "the grouped form streams M through a ring");
   static_assert(!(CX && (MR || MH || OP != kOpBF16)), "the complex form is split-BF16 with M rings");
   static_assert(!(MH && (MR || OP != kOpBF16)), "resident M_hi is a split-BF16 form of its own");
+  static_assert(W == 1 || (W == 2 && !G && !MR && !CX && !MH && OP == kOpBF16 && NXR == 2),
+                "wide tiles: single split-BF16 form, X 2 + M 2");
+  constexpr int WR = W * BR;                              // r of each plane per unit
+  constexpr uint32_t kXSt = W * kXStage;                  // bytes per X ring stage
   // X ring depth and the offset of the M region (ring or resident); the
   // epilogue staging area starts at the same offset in every configuration
   constexpr uint32_t kHalf = kMStage / 2;                 // one 128 x 64 bf16 box (hi or lo)
   constexpr uint32_t kMSt = CX ? 2 * kMStage : (MH ? kHalf : kMStage);   // bytes per M ring stage
   constexpr int NX = (MR || CX) ? 2 : (MH ? 3 : NXR);
-  constexpr int NM = MR ? kMRMaxChunks : (MH ? 2 : (int)((kPlOffEpi - NX * kXStage) / kMSt));
-  constexpr uint32_t kOffM = NX * kXStage;
+  constexpr int NM = MR ? kMRMaxChunks : (MH ? 2 : (int)((kPlOffEpi - NX * kXSt) / kMSt));
+  constexpr uint32_t kOffM = NX * kXSt;
   constexpr uint32_t kOffMlo = kOffM + kMRMaxChunks * kHalf;   // MH: the M_lo ring after the resident M_hi
   static_assert(NX >= 2 && NX <= kMaxRing && NM >= 2 && NM <= kMaxRing - (MH ? 1 : 0), "ring depths");
   static_assert((MH ? kOffMlo : kOffM) + NM * kMSt == kPlOffEpi, "shared memory layout");
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * BN));
+                 "r"(2 * W * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -204,18 +214,19 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
           mxl = &gd[pid].xlo;
         }
         const long long tile = lu / mbk;
-        const int r0 = (int)(tile * BR);
-        const int r1 = (int)(R + tile * BR);   // same r in the imaginary plane
+        const int r0 = (int)(tile * WR);
+        const int r1 = (int)(R + tile * WR);   // same r in the imaginary plane
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % NX);
           if (!mbar_wait(empty_x(s), ((g / NX) & 1) ^ 1, abort_flag, err, 11)) { ok = false; break; }
-          const uint32_t st = sbase + s * kXStage;
-          mbar_arrive_tx(full_x(s), kXStage);
+          const uint32_t st = sbase + s * kXSt;
+          mbar_arrive_tx(full_x(s), kXSt);
           constexpr int CK = chunk_k<OP>();
+          // boxes of WR rows: X_hi re | X_hi im | X_lo re | X_lo im
           tma_load_2d(st, mxh, kc * CK, r0, full_x(s));
-          tma_load_2d(st + 8192, mxh, kc * CK, r1, full_x(s));
-          tma_load_2d(st + 16384, mxl, kc * CK, r0, full_x(s));
-          tma_load_2d(st + 24576, mxl, kc * CK, r1, full_x(s));
+          tma_load_2d(st + W * 8192, mxh, kc * CK, r1, full_x(s));
+          tma_load_2d(st + W * 16384, mxl, kc * CK, r0, full_x(s));
+          tma_load_2d(st + W * 24576, mxl, kc * CK, r1, full_x(s));
         }
       }
       const uint32_t issued = g;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
     if (lane == 0) {
       // instruction descriptor: FP32 accumulator; A, B bf16 (1) or tf32 (2); K-major; N, M
       constexpr uint32_t kAB = OP == kOpBF16 ? 1u : 2u;
-      constexpr uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(BN >> 3) << 17) |
+      constexpr uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(W * BN >> 3) << 17) |
                                  ((uint32_t)(BM >> 4) << 24);
       constexpr uint32_t idesc64 = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(BR >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         const int a = t & 1;
         if (!mbar_wait(acc_empty(a), ((t >> 1) & 1) ^ 1, abort_flag, err, 13)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + a * BN;
+        const uint32_t d_tmem = tmem_base + a * W * BN;
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int sx = (int)(g % NX), sm = MR ? kc : (int)(g % NM);
           if (!MR && !mbar_wait(full_m(sm), (g / NM) & 1, abort_flag, err, 14)) { ok = false; break; }
@@ -317,7 +328,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
           tc_fence_after();
           const uint32_t ahi = MH ? sbase + kOffM + kc * kHalf : sbase + kOffM + sm * kMSt;
           const uint32_t alo = MH ? sbase + kOffMlo + sm * kMSt : ahi + 16384;
-          const uint32_t bhi = sbase + sx * kXStage, blo = bhi + 16384;
+          const uint32_t bhi = sbase + sx * kXSt, blo = bhi + W * 16384;
           // four k-steps of 32 bytes per 128-byte row (K = 16 bf16 or 8 tf32 each)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
@@ -373,19 +384,23 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
       }
       const long long tile = lu / mbk;
       const int mb = (int)(lu % mbk);
+      const int i_base = mb * BM + q * 32;
+#pragma unroll
+      for (int sb = 0; sb < W; ++sb) {   // 64-r sub-blocks of a wide tile
       uint32_t vr[2][16], vi[2][16];
 #pragma unroll
       for (int g2 = 0; g2 < 2; ++g2) {
-        const int cc = 2 * half + g2;
-        const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * BN + cc * 16;
+        const int cc = 4 * sb + 2 * half + g2;
+        const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + a * W * BN + cc * 16;
         tmem_ld16(tl, vr[g2]);
-        tmem_ld16(tl + BR, vi[g2]);
+        tmem_ld16(tl + W * BR, vi[g2]);
       }
       tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty(a));
-      const int i_base = mb * BM + q * 32;
+      if (sb == W - 1) {   // the accumulator goes back to the MMA warp after the last read
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty(a));
+      }
       if constexpr (OP != kOpBF16) {
         // FP32 boxes of 32 x 32 (128-byte rows), one at a time through the 4 KB
         // staging area: per component the hi words (kOpTF32F: the FP32 value),
@@ -427,7 +442,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
             __syncwarp();
           }
         }
-        continue;
+        continue;   // the TF32 forms have W == 1: on to the next unit
       }
       // this warp's two groups are adjacent (cc = 2 half, 2 half + 1): one 32 x 32 box
       // (64-byte rows) per component, real part first, then imaginary part
@@ -453,14 +468,15 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
-          const int x = (int)(tile * BR + 32 * half);
-          const uint32_t sb = smem_u32(box);
-          tma_store_3d(myh, sb, x, i_base, comp);
-          tma_store_3d(myl, sb + 2048, x, i_base, comp);
+          const int x = (int)(tile * WR + 64 * sb + 32 * half);
+          const uint32_t bs = smem_u32(box);
+          tma_store_3d(myh, bs, x, i_base, comp);
+          tma_store_3d(myl, bs + 2048, x, i_base, comp);
           bulk_commit();
         }
         __syncwarp();
       }
+      }   // sub-blocks
     }
     if (lane == 0) bulk_wait0();
   }
@@ -468,7 +484,8 @@ __global__ void __launch_bounds__(PL_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * BN));
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * W * BN));
 }
 
 }  // namespace b3

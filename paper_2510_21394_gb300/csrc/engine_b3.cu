@@ -88,8 +88,8 @@ void launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaSt
 // (all eligible configurations, on the handle's own work buffers, at setup) and
 // the fastest is used from then on.  FCGLE_PLAIN_CFG=<id> (read once) forces
 // one configuration where it is eligible.
-enum PlainCfg { kCfgX4M2 = 0, kCfgX3M3 = 1, kCfgX2M4 = 2, kCfgMR = 3, kCfgMH = 4, kNumPlainCfg = 5 };
-const char* const kPlainCfgName[kNumPlainCfg] = {"X4M2", "X3M3", "X2M4", "residentM", "residentMhi"};
+enum PlainCfg { kCfgX4M2 = 0, kCfgX3M3 = 1, kCfgX2M4 = 2, kCfgMR = 3, kCfgMH = 4, kCfgWide = 5, kNumPlainCfg = 6 };
+const char* const kPlainCfgName[kNumPlainCfg] = {"X4M2", "X3M3", "X2M4", "residentM", "residentMhi", "wide128"};
 
 using PlainKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
                              b3::KParams, const b3::PlainDesc*, int, long long);
@@ -100,6 +100,7 @@ PlainKernel plain_kernel(int cfg) {
     case kCfgX2M4: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2>;
     case kCfgMR: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, true>;
     case kCfgMH: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 3, false, false, true>;
+    case kCfgWide: return b3::mp_b3_plain_kernel<false, b3::kOpBF16, 2, false, false, false, 2>;
     default: return b3::mp_b3_plain_kernel<false>;
   }
 }
@@ -116,7 +117,7 @@ int forced_plain_cfg() {
 
 struct TuneEntry {
   int cfg = kCfgX4M2;
-  float us[kNumPlainCfg] = {-1.f, -1.f, -1.f, -1.f, -1.f};   // -1: not eligible
+  float us[kNumPlainCfg] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};   // -1: not eligible
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, long long>, TuneEntry> g_tune;   // (p, R)
@@ -1112,7 +1113,7 @@ class EngineB3 : public EngineBase {
       TuneEntry e;
       cfg = tuned_lookup(kp.p, R, e) ? e.cfg : default_plain_cfg(kp, units);
     }
-    launch_plain_cfg(cfg, txh, txl, m, tyh, tyl, kp, units);
+    launch_plain_cfg(cfg, xh, xl, txh, txl, m, tyh, tyl, kp, units);
   }
 
   // resident M: every CTA keeps one fixed i-block (grid a multiple of m_blocks)
@@ -1126,8 +1127,23 @@ class EngineB3 : public EngineBase {
     return kp.k_chunks <= b3::kMRMaxChunks && grid_mr(units, kp.m_blocks) >= kp.m_blocks;
   }
   static int default_plain_cfg(const b3::KParams&, long long) { return kCfgX4M2; }
-  void launch_plain_cfg(int cfg, const CUtensorMap& txh, const CUtensorMap& txl, const Mat& m, const CUtensorMap& tyh,
-                        const CUtensorMap& tyl, const b3::KParams& kp, long long units) {
+  // txh, txl: X maps with 64-row boxes (xh, xl: the same tensors, for the
+  // 128-row boxes of the wide configuration); kp, units: 64-r tiles
+  void launch_plain_cfg(int cfg, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const CUtensorMap& txh,
+                        const CUtensorMap& txl, const Mat& m, const CUtensorMap& tyh, const CUtensorMap& tyl,
+                        const b3::KParams& kp, long long units) {
+    if (cfg == kCfgWide) {
+      CUtensorMap wxh, wxl;
+      encode_bf16(&wxh, xh, (uint64_t)kp.p, 2 * (uint64_t)kp.R, 2 * b3::BR);
+      encode_bf16(&wxl, xl, (uint64_t)kp.p, 2 * (uint64_t)kp.R, 2 * b3::BR);
+      b3::KParams kw = kp;
+      kw.tiles = (kp.R + 2 * b3::BR - 1) / (2 * b3::BR);
+      const long long wunits = kw.tiles * kw.m_blocks;
+      launch_pdl(plain_kernel(cfg), (int)std::min<long long>(wunits, num_sms()), b3::PL_THREADS, b3::kPlSmemBytes,
+                 st_, wxh, wxl, m.tm_hi, m.tm_lo, tyh, tyl, kw, (const b3::PlainDesc*)nullptr, 0, 0LL);
+      FCGLE_LAUNCHED(launches);
+      return;
+    }
     const int grid = (cfg == kCfgMR || cfg == kCfgMH) ? grid_mr(units, kp.m_blocks)
                                                        : (int)std::min<long long>(units, num_sms());
     launch_pdl(plain_kernel(cfg), grid, b3::PL_THREADS, b3::kPlSmemBytes, st_, txh, txl, m.tm_hi, m.tm_lo, tyh, tyl,
@@ -1220,9 +1236,9 @@ class EngineB3 : public EngineBase {
         constexpr int kReps = 5;
         for (int c = 0; c < kNumPlainCfg; ++c) {
           if (!plain_cfg_ok(c, kp, units)) continue;
-          launch_plain_cfg(c, txh, txl, m, tyh, tyl, kp, units);   // warm-up
+          launch_plain_cfg(c, in.hi, in.lo, txh, txl, m, tyh, tyl, kp, units);   // warm-up
           FCGLE_CUDA(cudaEventRecord(e0, st_));
-          for (int r = 0; r < kReps; ++r) launch_plain_cfg(c, txh, txl, m, tyh, tyl, kp, units);
+          for (int r = 0; r < kReps; ++r) launch_plain_cfg(c, in.hi, in.lo, txh, txl, m, tyh, tyl, kp, units);
           FCGLE_CUDA(cudaEventRecord(e1, st_));
           FCGLE_CUDA(cudaEventSynchronize(e1));
           float ms = 0.f;

@@ -139,3 +139,47 @@ def test_precise_tf32_product_matches_fp64_kernel(fc, ns):
         fc.fcgle_mode_product(s32.h, 0, 1 | 2 | 4, X.float(), Y32)
     s64.close()
     s32.close()
+
+
+_FORCED_CHECK = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+from paper_2510_21394_gb300 import fcgle
+ns = [30, 134, 14]
+boxes = [(-4.0, 4.0), (-3.0, 3.0), (-5.0, 5.0)]
+al = [1.3, 1.7, 1.5]
+pars = (1.0, 0.4, 0.5, 1.0, 0.2)
+s64 = fcgle.Solver(ns, boxes, al, *pars, precision="fp64")
+s32 = fcgle.Solver(ns, boxes, al, *pars, precision="bf16x3")
+P = fcgle.fcgle_internal_elems(s32.h)
+gen = torch.Generator(device="cuda").manual_seed(3)
+X = torch.randn(2 * P, device="cuda", dtype=torch.float64, generator=gen)
+worst = 0.0
+for mu in range(3):
+    for fwd in (True, False):
+        Y64 = torch.empty_like(X)
+        Y32 = torch.empty(2 * P, device="cuda", dtype=torch.float32)
+        fcgle.fcgle_mode_product(s64.h, mu, fwd, X, Y64)
+        fcgle.fcgle_mode_product(s32.h, mu, fwd, X.float(), Y32)
+        s64.sync(); s32.sync()
+        d = Y32.double() - Y64
+        worst = max(worst, float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(Y64)),
+                    float(d.abs().max() / Y64.abs().max()))
+print("worst", worst)
+assert worst <= 3e-5, worst
+"""
+
+
+@pytest.mark.parametrize("cfg", range(6))
+def test_every_plain_configuration(fc, cfg):
+    """Each ring / tile configuration of the plain product, forced through
+    FCGLE_PLAIN_CFG (read once per process, hence a child process), against
+    the FP64 kernel; the autotuner only ever runs the fastest one."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FCGLE_PLAIN_CFG=str(cfg))
+    r = subprocess.run([sys.executable, "-c", _FORCED_CHECK.format(root=root)], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
