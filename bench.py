@@ -982,7 +982,8 @@ def run_mp_only(args):
         s = fcgle.Solver(C2_NS, C2_BOXES, C2_ALPHAS, **C2_PARS, precision=args.precision)
         dims = 2
     else:
-        s = fcgle.Solver([n] * 3, BOXES, ALPHAS, **PARS, precision=args.precision)
+        ns = [n, n, args.n3 or n]
+        s = fcgle.Solver(ns, BOXES, ALPHAS, **PARS, precision=args.precision)
         dims = 3
     P = fcgle.fcgle_internal_elems(s.h)
     if args.precision == "bf16x3":
@@ -992,9 +993,13 @@ def run_mp_only(args):
         X = torch.randn(2 * P, device="cuda", dtype=torch.float64)
         flags = 1
     Y = torch.empty_like(X)
+    # 3D split-BF16: also the slab-fused modes 1 + 2 and the natural-order mode 3
+    extra = [(0, flags | 8), (2, flags | 16)] if dims == 3 and args.precision == "bf16x3" else []
     for _ in range(args.mp_only):
         for d_ in range(dims):
             fcgle.fcgle_mode_product(s.h, d_, flags, X, Y)
+        for d_, fl in extra:
+            fcgle.fcgle_mode_product(s.h, d_, fl, X, Y)
     torch.cuda.synchronize()
     s.sync()
     s.close()
@@ -1020,6 +1025,8 @@ def main():
     ap.add_argument("--cpu-sample-2d", nargs=3, default=None)
     ap.add_argument("--mp-only", type=int, default=0, metavar="REPS",
                     help="only run REPS x 3 raw mode products (all directions) of the n^3 workload (profiling)")
+    ap.add_argument("--n3", type=int, default=None,
+                    help="--mp-only, cube workload: third extent (default n), for profiling a smaller case")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--scheme", default="krogstad", choices=sorted(SCHEME_NAMES),
                     help="cube workload: time-stepping scheme (default krogstad, the benchmark)")
