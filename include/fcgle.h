@@ -181,8 +181,11 @@ fcgle_status fcgle_set_exp_form(fcgle_handle h, int form);
  * the form the autotuner found faster for the handle's extents (see
  * fcgle_autotune_report).  The two forms round differently (both at the
  * split-BF16 level); the first and last Tucker operators of a time
- * integration (the precise split-TF32 transforms) and batches always use the
- * rotating form.  Other handles (FP64, d != 3) accept FCGLE_TUCKER_AUTO and
+ * integration (the precise split-TF32 transforms) and the grouped launches of
+ * a batch always use the rotating form; fcgle_batch_create sets its instance
+ * handles to FCGLE_TUCKER_ROTATING as well, so that every path of a batch
+ * rounds alike (fcgle_set_tucker_form on an instance changes its own
+ * per-instance launches only).  Other handles (FP64, d != 3) accept FCGLE_TUCKER_AUTO and
  * FCGLE_TUCKER_ROTATING and run their only form; FCGLE_TUCKER_SLAB gives
  * FCGLE_ERR_UNSUPPORTED there.  Any other value: FCGLE_ERR_INVALID_ARG. */
 typedef enum { FCGLE_TUCKER_AUTO = 0, FCGLE_TUCKER_ROTATING = 1, FCGLE_TUCKER_SLAB = 2 } fcgle_tucker_form;

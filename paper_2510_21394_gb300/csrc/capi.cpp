@@ -468,6 +468,10 @@ fcgle_status fcgle_batch_create(int count, const fcgle_params* params, void* cud
               h->prm = params[i];
               h->stream = b->streams[b->stream_of[i]];
               h->eng = make_engine(params[i], h->stream);
+              // the grouped launches run every Tucker operator in the rotating
+              // form; the instances' own launches use it too, so that every path
+              // of a batch rounds alike
+              h->eng->set_tucker_form(FCGLE_TUCKER_ROTATING);
               b->inst[i] = h;
             } catch (const std::exception& e) {
               errs[i] = e.what();

@@ -1165,7 +1165,7 @@ class EngineB3 : public EngineBase {
   // rotating form and in the slab-fused form, once per process per shape,
   // and keeps the slab-fused form where it is clearly faster.
   void tune_slab() {
-    if (!slab_ok()) return;
+    if (!slab_ok() || tucker_form_ != FCGLE_TUCKER_AUTO) return;
     const auto key = std::make_tuple(s_.p[0], s_.p[1], s_.p[2]);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
