@@ -22,6 +22,8 @@ KERNEL_SHAPES = [
     [30, 22, 134],   # p = (32, 24, 136): N2 = 32 (one output box, idle store warps), 3 ragged k-chunks in direction 3
     [134, 150, 6],   # p = (136, 152, 8): 2 i1-blocks (ragged), N2 = 160 > p2, two M2 boxes, ragged k-chunks
     [256, 256, 8],   # p = (256, 256, 8): the full 256 x 256 slab
+    [302, 22, 6],    # p = (304, 24, 8): three i1-blocks (the last ragged), ten 32-wide k-chunks in stage 1
+    [14, 6, 518],    # p = (16, 8, 520): N2 = 16, one partly valid output box; mode 3 with five ragged i-blocks
 ]
 BOXES = [(-4.0, 4.0), (-3.0, 3.0), (-5.0, 5.0)]
 AL = [1.3, 1.7, 1.5]
@@ -140,7 +142,7 @@ def _host(t):
     return t.cpu().numpy().astype(np.complex128)
 
 
-@pytest.mark.parametrize("ns", [[33, 20, 29], [134, 150, 6], [40, 256, 24]])
+@pytest.mark.parametrize("ns", [[33, 20, 29], [134, 150, 6], [40, 256, 24], [302, 22, 6]])
 def test_apply_f_slab_form(fc, ns):
     P = tensor.Problem(ns, BOXES, AL, *PARS.values())
     S = tensor.Spectral(P)
