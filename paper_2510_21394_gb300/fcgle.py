@@ -353,7 +353,9 @@ def fcgle_internal_elems(h):
 
 def fcgle_mode_product(h, direction, forward, X, Y):
     """X, Y: flat device tensors in the internal layout: 2 P reals (float64 / float32), or with
-    forward bit 1 set (BF16X3 handles) 4 P bf16 (hi planes, then lo planes)."""
+    bit 1 of `forward` (the C flags) set (BF16X3 handles) 4 P bf16 (hi planes, then lo planes).
+    Bit 0 forward (Q^T), bit 2 the precise split-TF32 product (FP32 in and out), bit 3 the
+    slab-fused modes 1 + 2 (3D, direction 0), bit 4 the last direction on a natural-order input."""
     _check(_lib.fcgle_mode_product(h, int(direction), int(forward), _ptr(X), _ptr(Y)))
 
 
