@@ -38,8 +38,10 @@ SLAB_SAVED_BYTES_PER_ELEM = 8 * 16   # slab-fused modes 1 + 2: one 16-byte pass 
 
 
 def tucker_form_of(report, n):
-    """'slab-fused' or 'rotating': the autotuner's choice for an n^3 handle."""
-    m = re.search(r"tucker p=\(%d,%d,%d\):.*-> (\S+)" % (n, n, n), report)
+    """'slab-fused' or 'rotating': the autotuner's choice for an n^3 split-BF16
+    handle (its extents are n rounded up to a multiple of 8)."""
+    p = (n + 7) // 8 * 8
+    m = re.search(r"tucker p=\(%d,%d,%d\):.*-> (\S+)" % (p, p, p), report)
     return m.group(1) if m else "rotating"
 
 # 2D 1023 x 1024 workload (linearly-implicit Euler and ETD2RK, 500 steps): the
@@ -475,8 +477,9 @@ def run_ours(args, rank, world, local_rank):
                   "peak_kind": f"{peak_kind} hbm_gbs (burst)", "launch_ms": round(mp_ms, 4), "algorithmic_bytes": mp_bytes}
     # ---- the slab-fused mode-1 + mode-2 product and the natural-order mode-3 product
     form = tucker_form_of(fcgle.fcgle_autotune_report(), n)
+    slab_eligible = (n + 7) // 8 * 8 <= 256      # the slab kernel needs p_2 <= 256
     timed = {}
-    for name, d_, fl in (("slab12", 0, 1 | 2 | 8), ("mn3", 2, 1 | 2 | 16)):
+    for name, d_, fl in ((("slab12", 0, 1 | 2 | 8), ("mn3", 2, 1 | 2 | 16)) if slab_eligible else ()):
         fcgle.fcgle_mode_product(solver.h, d_, fl, X, Y)
         torch.cuda.synchronize()
         k0.record(stream)
@@ -487,21 +490,24 @@ def run_ours(args, rank, world, local_rank):
         solver.sync()
         timed[name] = k0.elapsed_time(k1) / reps
     # FLOPs of the slab kernel: two mode products, 3 split passes, 2 p flops per real element
-    sl_flops = 2 * 3 * 2 * n * 2 * P
+    sl_flops = 2 * 3 * 2 * ((n + 7) // 8 * 8) * 2 * P
     bf_peak, _, bf_kind = measured_bf16_peak()
-    sl_tf = sl_flops / (timed["slab12"] / 1e3) / 1e12
-    slab_roof = {"bound": "tensor", "achieved": round(sl_tf, 1), "peak": bf_peak, "unit": "TFLOP/s",
-                 "frac": round(sl_tf / bf_peak, 4),
-                 "traffic": ncu_traffic(n, "mp_b3_slab12_256cube.md", SLAB_SOURCES),
-                 "kernel": "mp_b3_slab12_kernel (modes 1 + 2 of a 256^3 Tucker operator, split in/out)",
-                 "peak_kind": f"{bf_kind} bf16_tflops (burst)", "launch_ms": round(timed["slab12"], 4),
-                 "algorithmic_flops": sl_flops, "algorithmic_bytes": mp_bytes,
-                 "hbm_frac": round(mp_bytes / (timed["slab12"] / 1e3) / 1e9 / peak, 4)}
-    mn_gbs = mp_bytes / (timed["mn3"] / 1e3) / 1e9
-    mn_roof = {"bound": "hbm", "achieved": round(mn_gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(mn_gbs / peak, 4),
-               "kernel": "mp_b3_kernel<EpiStoreSplitGen, natural order> (mode 3 on the slab kernel's output)",
-               "launch_ms": round(timed["mn3"], 4), "algorithmic_bytes": mp_bytes}
-    roofline = slab_roof if form == "slab-fused" else plain_roof
+    slab_roof = mn_roof = None
+    if slab_eligible:
+        sl_tf = sl_flops / (timed["slab12"] / 1e3) / 1e12
+        slab_roof = {"bound": "tensor", "achieved": round(sl_tf, 1), "peak": bf_peak, "unit": "TFLOP/s",
+                     "frac": round(sl_tf / bf_peak, 4),
+                     "traffic": ncu_traffic(n, "mp_b3_slab12_256cube.md", SLAB_SOURCES),
+                     "kernel": f"mp_b3_slab12_kernel (modes 1 + 2 of a {n}^3 Tucker operator, split in/out)",
+                     "peak_kind": f"{bf_kind} bf16_tflops (burst)", "launch_ms": round(timed["slab12"], 4),
+                     "algorithmic_flops": sl_flops, "algorithmic_bytes": mp_bytes,
+                     "hbm_frac": round(mp_bytes / (timed["slab12"] / 1e3) / 1e9 / peak, 4)}
+        mn_gbs = mp_bytes / (timed["mn3"] / 1e3) / 1e9
+        mn_roof = {"bound": "hbm", "achieved": round(mn_gbs, 1), "peak": peak, "unit": "GB/s",
+                   "frac": round(mn_gbs / peak, 4),
+                   "kernel": "mp_b3_kernel<EpiStoreSplitGen, natural order> (mode 3 on the slab kernel's output)",
+                   "launch_ms": round(timed["mn3"], 4), "algorithmic_bytes": mp_bytes}
+    roofline = slab_roof if (form == "slab-fused" and slab_roof) else plain_roof
     del X, Y
     # ---- the precise end-transform product (split-TF32 on the tensor cores, FP32 in and out:
     # the split pass 24 B + the product 24 B per complex element), per launch pair
