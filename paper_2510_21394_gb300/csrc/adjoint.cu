@@ -133,25 +133,6 @@ __device__ __forceinline__ bool lam_sum(const LD& L, size_t q, double& s) {
 }
 
 template <typename T>
-__global__ void scale_exp_kernel(size_t P, LD L, double cre, double cim, const T* __restrict__ x, T* __restrict__ y) {
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
-    double s;
-    const bool valid = lam_sum(L, q, s);
-    double er = 0.0, ei = 0.0;
-    if (valid) {
-      double sn, cs;
-      sincos(cim * s, &sn, &cs);
-      const double m = exp(cre * s);
-      er = m * cs;
-      ei = m * sn;
-    }
-    const double xr = x[q], xi = x[P + q];
-    y[q] = (T)(er * xr - ei * xi);
-    y[P + q] = (T)(er * xi + ei * xr);
-  }
-}
-
-template <typename T>
 __global__ void spec_dot_kernel(size_t P, LD L, const T* __restrict__ x, const T* __restrict__ y, double* acc) {
   double v[2] = {0.0, 0.0};
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
@@ -169,6 +150,56 @@ __global__ void axpby_kernel(size_t n, double a, const T* __restrict__ x1, doubl
                              T* __restrict__ y) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
     y[q] = (T)(a * (double)x1[q] + (x2 ? b * (double)x2[q] : 0.0));
+}
+
+// e^{z} with z = (cre + i cim) s at an element (0 on padding)
+__device__ __forceinline__ void exp_z(const LD& L, size_t q, double cre, double cim, double& er, double& ei) {
+  double s;
+  er = ei = 0.0;
+  if (lam_sum(L, q, s)) {
+    double sn, cs;
+    sincos(cim * s, &sn, &cs);
+    const double m = exp(cre * s);
+    er = m * cs;
+    ei = m * sn;
+  }
+}
+
+// y1 = e^z (x + c1 k), y2 = e^z (x + c2 k): the two stage values of a
+// Lawson-RK2 step (V^ and W^), one pass over x and k
+template <typename T>
+__global__ void exp_pair_kernel(size_t P, LD L, double cre, double cim, const T* __restrict__ x,
+                                const T* __restrict__ k, double c1, double c2, T* __restrict__ y1, T* __restrict__ y2) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    double er, ei;
+    exp_z(L, q, cre, cim, er, ei);
+    const double xr = x[q], xi = x[P + q], kr = k[q], ki = k[P + q];
+    double ur = xr + c1 * kr, ui = xi + c1 * ki;
+    y1[q] = (T)(er * ur - ei * ui);
+    y1[P + q] = (T)(er * ui + ei * ur);
+    ur = xr + c2 * kr;
+    ui = xi + c2 * ki;
+    y2[q] = (T)(er * ur - ei * ui);
+    y2[P + q] = (T)(er * ui + ei * ur);
+  }
+}
+
+// a = e^{z} x, b = e^{z} m (z already conjugated by the caller):
+// y = ca a + cb b and sum = a + b, one pass; y may alias x
+template <typename T>
+__global__ void exp_combo_kernel(size_t P, LD L, double cre, double cim, const T* x, const T* __restrict__ m,
+                                 double ca, double cb, T* y, T* __restrict__ sum) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x) {
+    double er, ei;
+    exp_z(L, q, cre, cim, er, ei);
+    const double xr = x[q], xi = x[P + q], mr = m[q], mi = m[P + q];
+    const double ar = er * xr - ei * xi, ai = er * xi + ei * xr;
+    const double br = er * mr - ei * mi, bi = er * mi + ei * mr;
+    y[q] = (T)(ca * ar + cb * br);
+    y[P + q] = (T)(ca * ai + cb * bi);
+    sum[q] = (T)(ar + br);
+    sum[P + q] = (T)(ai + bi);
+  }
 }
 
 // ---- FP32 forms (split-BF16 engine): per-element arithmetic in FP32 with
@@ -249,34 +280,79 @@ __global__ void gv_kernel_f(uint32_t P, GP g, const float* __restrict__ z, const
   block_acc<3>(v, acc, ADJ_GAMMA);
 }
 
-// y = e^{z} x with z = (ar + i ai) s, formed as x + (e^z - 1) x where
-// e^z - 1 = expm1(Re z) cos(Im z) - 2 sin^2(Im z / 2) + i e^{Re z} sin(Im z):
-// the FP32 rounding then falls on the correction, not on a factor that the
-// sweeps apply again every step.  Padding (j >= n) gives y = 0.
-__global__ void scale_exp_kernel_f(uint32_t P, LD L, float ar, float ai, const float* __restrict__ x,
-                                   float* __restrict__ y) {
+// e^z - 1 = mr + i mi at element v of a quad, z = (ar + i ai) s:
+// expm1(Re z) cos(Im z) - 2 sin^2(Im z / 2) + i e^{Re z} sin(Im z), so that a
+// product e^z x is formed as x + (e^z - 1) x and the FP32 rounding falls on the
+// correction, not on a factor that the sweeps apply again every step.
+// Padding (j >= n): e^z = 0, i.e. mr = -1, mi = 0.
+__device__ __forceinline__ void expm1_z_f(const Quad& Q, int v, float ar, float ai, float& mr, float& mi) {
+  mr = -1.f;
+  mi = 0.f;
+  if (Q.valid[v]) {
+    const float a = ar * Q.s[v], b = ai * Q.s[v];
+    float sn, cs, sh, ch;
+    sincosf(b, &sn, &cs);
+    sincosf(0.5f * b, &sh, &ch);
+    const float em = expm1f(a);
+    mr = em * cs - 2.f * sh * sh;
+    mi = (1.f + em) * sn;
+  }
+}
+
+// y1 = e^z (x + c1 k), y2 = e^z (x + c2 k) (FP32 form of exp_pair_kernel)
+__global__ void exp_pair_kernel_f(uint32_t P, LD L, float ar, float ai, const float* __restrict__ x,
+                                  const float* __restrict__ k, float c1, float c2, float* __restrict__ y1,
+                                  float* __restrict__ y2) {
   for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
     const Quad Q = quad_lam(L, q);
-    float xr[4], xi[4], yr[4], yi[4];
+    float xr[4], xi[4], kr[4], ki[4], pr[4], pi[4], wr[4], wi[4];
     ld4f(x + q, xr);
     ld4f(x + P + q, xi);
+    ld4f(k + q, kr);
+    ld4f(k + P + q, ki);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float mr = -1.f, mi = 0.f;
-      if (Q.valid[v]) {
-        const float a = ar * Q.s[v], b = ai * Q.s[v];
-        float sn, cs, sh, ch;
-        sincosf(b, &sn, &cs);
-        sincosf(0.5f * b, &sh, &ch);
-        const float em = expm1f(a);
-        mr = em * cs - 2.f * sh * sh;
-        mi = (1.f + em) * sn;
-      }
-      yr[v] = xr[v] + (mr * xr[v] - mi * xi[v]);
-      yi[v] = xi[v] + (mr * xi[v] + mi * xr[v]);
+      float mr, mi;
+      expm1_z_f(Q, v, ar, ai, mr, mi);
+      const float ur = xr[v] + c1 * kr[v], ui = xi[v] + c1 * ki[v];
+      pr[v] = ur + (mr * ur - mi * ui);
+      pi[v] = ui + (mr * ui + mi * ur);
+      const float vr = xr[v] + c2 * kr[v], vi = xi[v] + c2 * ki[v];
+      wr[v] = vr + (mr * vr - mi * vi);
+      wi[v] = vi + (mr * vi + mi * vr);
+    }
+    st4f(y1 + q, pr);
+    st4f(y1 + P + q, pi);
+    st4f(y2 + q, wr);
+    st4f(y2 + P + q, wi);
+  }
+}
+
+// a = e^z x, b = e^z m; y = ca a + cb b, sum = a + b (FP32 form of exp_combo_kernel; y may alias x)
+__global__ void exp_combo_kernel_f(uint32_t P, LD L, float ar, float ai, const float* x, const float* __restrict__ m,
+                                   float ca, float cb, float* y, float* __restrict__ sum) {
+  for (uint32_t q = 4 * (blockIdx.x * blockDim.x + threadIdx.x); q < P; q += 4 * gridDim.x * blockDim.x) {
+    const Quad Q = quad_lam(L, q);
+    float xr[4], xi[4], nr[4], ni[4], yr[4], yi[4], sr[4], si[4];
+    ld4f(x + q, xr);
+    ld4f(x + P + q, xi);
+    ld4f(m + q, nr);
+    ld4f(m + P + q, ni);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float mr, mi;
+      expm1_z_f(Q, v, ar, ai, mr, mi);
+      const float a_r = xr[v] + (mr * xr[v] - mi * xi[v]), a_i = xi[v] + (mr * xi[v] + mi * xr[v]);
+      const float b_r = nr[v] + (mr * nr[v] - mi * ni[v]), b_i = ni[v] + (mr * ni[v] + mi * nr[v]);
+      yr[v] = ca * a_r + cb * b_r;
+      yi[v] = ca * a_i + cb * b_i;
+      sr[v] = a_r + b_r;
+      si[v] = a_i + b_i;
     }
     st4f(y + q, yr);
     st4f(y + P + q, yi);
+    st4f(sum + q, sr);
+    st4f(sum + P + q, si);
   }
 }
 
@@ -348,17 +424,6 @@ void adj_gu(const Shape& s, const GParams& gp, const T* u, const T* la, const T*
   FCGLE_LAUNCHED(nl);
 }
 template <typename T>
-void adj_scale_exp(const Shape& s, const LamVecs& lv, double theta, bool conj, const T* x, T* y, cudaStream_t st,
-                   long long& nl) {
-  if constexpr (std::is_same<T, float>::value)
-    scale_exp_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
-                                                      (float)((conj ? -1.0 : 1.0) * theta * lv.c_im), x, y);
-  else
-    scale_exp_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re,
-                                                        (conj ? -1.0 : 1.0) * theta * lv.c_im, x, y);
-  FCGLE_LAUNCHED(nl);
-}
-template <typename T>
 void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, double* acc, cudaStream_t st,
                   long long& nl) {
   if constexpr (std::is_same<T, float>::value)
@@ -376,17 +441,42 @@ void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* 
   FCGLE_LAUNCHED(nl);
 }
 
+template <typename T>
+void adj_exp_pair(const Shape& s, const LamVecs& lv, double theta, const T* x, const T* k, double c1, double c2,
+                  T* y1, T* y2, cudaStream_t st, long long& nl) {
+  if constexpr (std::is_same<T, float>::value)
+    exp_pair_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
+                                                     (float)(theta * lv.c_im), x, k, (float)c1, (float)c2, y1, y2);
+  else
+    exp_pair_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re, theta * lv.c_im, x, k,
+                                                       c1, c2, y1, y2);
+  FCGLE_LAUNCHED(nl);
+}
+template <typename T>
+void adj_exp_h_combo(const Shape& s, const LamVecs& lv, double theta, const T* x, const T* m, double ca, double cb,
+                     T* y, T* sum, cudaStream_t st, long long& nl) {
+  if constexpr (std::is_same<T, float>::value)
+    exp_combo_kernel_f<<<grid_of(s.P / 4), 256, 0, st>>>((uint32_t)s.P, make_ld(s, lv), (float)(theta * lv.c_re),
+                                                      (float)(-theta * lv.c_im), x, m, (float)ca, (float)cb, y, sum);
+  else
+    exp_combo_kernel<T><<<grid_of(s.P), 256, 0, st>>>(s.P, make_ld(s, lv), theta * lv.c_re, -theta * lv.c_im, x, m,
+                                                        ca, cb, y, sum);
+  FCGLE_LAUNCHED(nl);
+}
+
 #define INST(T)                                                                                                  \
   template void adj_misfit<T>(const Shape&, const T*, const T*, T*, double*, cudaStream_t, long long&);          \
   template void adj_gv<T>(const Shape&, const GParams&, const T*, const T*, double, T*, double*, cudaStream_t,  \
                           long long&);                                                                          \
   template void adj_gu<T>(const Shape&, const GParams&, const T*, const T*, const T*, double, double, T*,       \
                           double*, cudaStream_t, long long&);                                                   \
-  template void adj_scale_exp<T>(const Shape&, const LamVecs&, double, bool, const T*, T*, cudaStream_t,        \
-                                 long long&);                                                                   \
   template void adj_spec_dot<T>(const Shape&, const LamVecs&, const T*, const T*, double*, cudaStream_t,        \
                                 long long&);                                                                    \
-  template void adj_axpby<T>(const Shape&, double, const T*, double, const T*, T*, cudaStream_t, long long&);
+  template void adj_axpby<T>(const Shape&, double, const T*, double, const T*, T*, cudaStream_t, long long&);    \
+  template void adj_exp_pair<T>(const Shape&, const LamVecs&, double, const T*, const T*, double, double, T*, T*, \
+                                cudaStream_t, long long&);                                                       \
+  template void adj_exp_h_combo<T>(const Shape&, const LamVecs&, double, const T*, const T*, double, double, T*,  \
+                                   T*, cudaStream_t, long long&);
 INST(float)
 INST(double)
 #undef INST

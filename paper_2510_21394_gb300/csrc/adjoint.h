@@ -54,11 +54,6 @@ template <typename T>
 void adj_gu(const Shape& s, const GParams& gp, const T* u, const T* la, const T* lb, double ca, double cb, T* out,
             double* acc, cudaStream_t st, long long& nl);
 
-// y = e^{theta (nu +/- i eta) lam} o x (conj selects the minus sign), evaluated in FP64
-template <typename T>
-void adj_scale_exp(const Shape& s, const LamVecs& lv, double theta, bool conj, const T* x, T* y, cudaStream_t st,
-                   long long& nl);
-
 // acc[Z_RE, Z_IM] += sum conj(x) Lam_D y  (Lam_D from the lam_mu vectors, weight 1)
 template <typename T>
 void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, double* acc, cudaStream_t st,
@@ -67,6 +62,17 @@ void adj_spec_dot(const Shape& s, const LamVecs& lv, const T* x, const T* y, dou
 // y = a x1 + b x2 (real coefficients; x2 may be null)
 template <typename T>
 void adj_axpby(const Shape& s, double a, const T* x1, double b, const T* x2, T* y, cudaStream_t st, long long& nl);
+
+// y1 = E (x + c1 k), y2 = E (x + c2 k) with E = e^{theta (nu + i eta) Lam} (FP64
+// exp / sincos, or the FP32 expm1 form), one pass
+template <typename T>
+void adj_exp_pair(const Shape& s, const LamVecs& lv, double theta, const T* x, const T* k, double c1, double c2,
+                  T* y1, T* y2, cudaStream_t st, long long& nl);
+
+// with a = E^H x, b = E^H m: y = ca a + cb b (y may alias x) and sum = a + b, one pass
+template <typename T>
+void adj_exp_h_combo(const Shape& s, const LamVecs& lv, double theta, const T* x, const T* m, double ca, double cb,
+                     T* y, T* sum, cudaStream_t st, long long& nl);
 
 // Driver.  Eng provides: Shape shape(); cudaStream_t stream(); long long& nlaunch();
 // GParams gparams(); LamVecs lamvecs(); T* alloc(size_t n) (freed by the caller afterwards);
@@ -117,10 +123,8 @@ void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, 
     e.tuckerT(x1, x2, true);                                                     // K^
     T* vh = keep_vh ? keep_vh : a;
     T* wh = keep_wh ? keep_wh : b;
-    adj_axpby<T>(s, 1.0, uh, tau, x2, x1, st, nl);
-    adj_scale_exp<T>(s, lv, tau, false, x1, vh, st, nl);                         // V^ = E(U^ + tau K^)
-    adj_axpby<T>(s, 1.0, uh, 0.5 * tau, x2, x1, st, nl);
-    adj_scale_exp<T>(s, lv, tau, false, x1, wh, st, nl);                         // W^ = E(U^ + tau/2 K^)
+    // V^ = E(U^ + tau K^), W^ = E(U^ + tau/2 K^)
+    adj_exp_pair<T>(s, lv, tau, uh, x2, tau, 0.5 * tau, vh, wh, st, nl);
     T* v = keep_v ? keep_v : x1;
     e.tuckerT(vh, v, false);                                                     // v = bwd(V^)
     gcombo<T>(s, gp0, t + tau, v, nullptr, nullptr, 1, 0, 0, 0, 1, 0, y, st, nl);   // g(t + tau, v)
@@ -150,14 +154,12 @@ void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, 
       adj_gv<T>(s, gp0, sv[j], y, 0.5 * tau, mv, acc, st, nl);  // m_v = (D_v g)^* (tau/2 bwd(m^'))
       e.tuckerT(mv, x1, true);                                 // m^_V
       adj_spec_dot<T>(s, lv, x1, svh[j], acc, st, nl);        // Z += conj(m^_V) Lam_D V^
-      adj_scale_exp<T>(s, lv, tau, true, x1, a, st, nl);      // a = E^H m^_V
-      adj_scale_exp<T>(s, lv, tau, true, mh, b, st, nl);      // b = E^H m^'
-      adj_axpby<T>(s, tau, a, 0.5 * tau, b, x1, st, nl);      // tau a + tau/2 b
+      // with a = E^H m^_V and b = E^H m^': x1 = tau a + tau/2 b, a <- a + b
+      adj_exp_h_combo<T>(s, lv, tau, x1, mh, tau, 0.5 * tau, x1, a, st, nl);
       e.tuckerT(x1, y, false);
       adj_gv<T>(s, gp0, su[j], y, 1.0, mv, acc, st, nl);      // (D_u g)^* bwd(tau a + tau/2 b)
       e.tuckerT(mv, x2, true);
-      adj_axpby<T>(s, 1.0, a, 1.0, b, x1, st, nl);
-      adj_axpby<T>(s, 1.0, x1, 1.0, x2, mh, st, nl);          // m^ = a + b + fwd(...)
+      adj_axpby<T>(s, 1.0, a, 1.0, x2, mh, st, nl);           // m^ = a + b + fwd(...)
     }
   }
   e.tuckerT_precise(mh, grad_u0, false);            // dJ/du_0 = bwd(m^_0)
