@@ -77,7 +77,8 @@ void adj_exp_h_combo(const Shape& s, const LamVecs& lv, double theta, const T* x
 // Driver.  Eng provides: Shape shape(); cudaStream_t stream(); long long& nlaunch();
 // GParams gparams(); LamVecs lamvecs(); T* alloc(size_t n) (freed by the caller afterwards);
 // void tuckerT(const T* X, T* Y, bool fwd) and tuckerT_precise(...) on planar
-// tensors (X, Y distinct).
+// tensors (X, Y distinct); void g_roundtrip(Uh, U, K, tmp, t): U = bwd(Uh),
+// K = fwd(g(t, U)) (tmp: a work tensor the engine may use; all distinct).
 template <typename T, class Eng>
 void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, const T* target, int C, T* grad_u0,
                         double* grad_params, double* loss) {
@@ -118,17 +119,13 @@ void adjoint_lawson_rk2(Eng& e, double tau, int nsteps, double t0, const T* u0, 
   // one forward step on the spectral state uh, optionally keeping u_n, v_n, V^_n, W^_n
   auto fstep = [&](double t, T* keep_u, T* keep_v, T* keep_vh, T* keep_wh) {
     T* uu = keep_u ? keep_u : u;
-    e.tuckerT(uh, uu, false);                                                    // u = bwd(U^)
-    gcombo<T>(s, gp0, t, uu, nullptr, nullptr, 1, 0, 0, 0, 1, 0, x1, st, nl);   // k1 = g(t, u)
-    e.tuckerT(x1, x2, true);                                                     // K^
+    e.g_roundtrip(uh, uu, x2, x1, t);                                            // u = bwd(U^), K^ = fwd(g(t, u))
     T* vh = keep_vh ? keep_vh : a;
     T* wh = keep_wh ? keep_wh : b;
     // V^ = E(U^ + tau K^), W^ = E(U^ + tau/2 K^)
     adj_exp_pair<T>(s, lv, tau, uh, x2, tau, 0.5 * tau, vh, wh, st, nl);
     T* v = keep_v ? keep_v : x1;
-    e.tuckerT(vh, v, false);                                                     // v = bwd(V^)
-    gcombo<T>(s, gp0, t + tau, v, nullptr, nullptr, 1, 0, 0, 0, 1, 0, y, st, nl);   // g(t + tau, v)
-    e.tuckerT(y, x2, true);
+    e.g_roundtrip(vh, v, x2, y, t + tau);                                       // v = bwd(V^), fwd(g(t + tau, v))
     adj_axpby<T>(s, 1.0, wh, 0.5 * tau, x2, uh, st, nl);                         // U^' = W^ + tau/2 fwd(g)
   };
 

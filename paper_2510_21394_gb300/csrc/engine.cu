@@ -292,6 +292,12 @@ class Engine : public EngineBase {
   void release_all() { adj_mem_.clear(); }
   void tuckerT(const T* X, T* Y, bool fwd) { tucker(X, Y, fwd); }
   void tuckerT_precise(const T* X, T* Y, bool fwd) { tucker(X, Y, fwd); }
+  // U = bwd(Uh), K = fwd(g(t, U)); tmp: a work tensor of 2 P
+  void g_roundtrip(const T* Uh, T* U, T* K, T* tmp, double t) {
+    tucker(Uh, U, false);
+    gcombo<T>(s_, gp_, t, U, nullptr, nullptr, 1, 0, 0, 0, 1, 0, tmp, st_, launches);
+    tucker(tmp, K, true);
+  }
 
   void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
                void* grad_u0, double* grad_params, double* loss) override {

@@ -734,6 +734,16 @@ class EngineB3 : public EngineBase {
     tucker(V, fwd, b3::EpiStoreF32{P32(), Y});
   }
   void tuckerT_precise(const float* X, float* Y, bool fwd) { tucker_f32(X, Y, fwd, false); }
+  // U = bwd(Uh) (FP32) and K = fwd(g(t, U)): g is evaluated in the epilogue of
+  // the backward operator, which also writes it split for the forward one
+  // (no standalone g pass, no split pass); tmp is not needed here
+  void g_roundtrip(const float* Uh, float* U, float* K, float*, double t) {
+    SplitOut V = SP(kV), G = SP(kW);
+    to_split_kernel<<<grid_for(P_ / 2), 256, 0, st_>>>(2 * P32(), Uh, V);
+    FCGLE_LAUNCHED(launches);
+    tucker(V, false, b3::EpiUpdateG{P32(), U, 0, gs_, gtime(t), 0.f, 1.f, G});
+    tucker(G, true, b3::EpiStoreF32{P32(), K});
+  }
 
   void adjoint(int scheme, double tau, int nsteps, double t0, const void* u0, const void* target, int ckpt,
                void* grad_u0, double* grad_params, double* loss) override {
